@@ -1,0 +1,203 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the oracle checks.
+
+This module only draws random numbers with the distributions of the
+workloads below; it holds none of the query method's arithmetic (no
+distance, no search, no verification).  Every draw comes from a
+``numpy.random.default_rng`` stream (PCG64), whose output does not depend
+on the host architecture, so x86 and Arm hosts produce identical arrays.
+
+Streams for a workload with seed ``s``:
+  s     base vectors
+  s+1   query vectors
+  s+2   per-query p, k and ef
+  s+3   HNSW levels of the L1 graph (G1)
+  s+4   HNSW levels of the L2 graph (G2)
+
+The HNSW level of each node is a random draw of the index construction
+(level = floor(-ln(U) * mL), mL = 1/ln(M), U uniform in (0, 1]); it is drawn
+here and passed to both graph builders as an input.
+
+Workloads (synthetic stand-ins for the paper's datasets, Table 1; no
+dataset item is reproduced):
+  mixture10k   N=10,000 d=32 Gaussian mixture, 16 centres ~ N(0, 4I),
+               points = centre + N(0, I); 100 queries from the mixture;
+               p ~ U(0.5, 2]; k=10; M=16, efConstruction=100; ef=64.
+  sift1m       N=1,000,000 d=128 integer features 0..255 (SIFT-shaped):
+               1,000 centres with per-dimension Exp(mean 30) clipped to
+               [0, 255]; x = round(clip(centre + N(0, 20^2), 0, 255));
+               10,000 queries from the same generator; p on the grid
+               {0.5, 0.6, ..., 2.0}; k=10; M=32, efConstruction=200.
+  sift1m_fp16  sift1m's base and queries, p ~ U(0.5, 2]; the traversal copy
+               is FP16 (0..255 is exact in FP16).
+  gist1m       N=1,000,000 d=960 in [0, 1] (GIST-shaped): 100 clusters,
+               centre mu ~ Beta(2, 5) per dimension, x ~ Beta(20 mu,
+               20 (1 - mu)); p ~ U(0.5, 2]; k in {1, 10, 100}; ef in
+               {32, 64, 128, 256, 512} with ef >= k; BF16 traversal copy.
+  unit10m      N=10,000,000 d=96 N(0, I) rows scaled to unit L2 norm, FP16;
+               p ~ U(0.5, 2]; k in {10, 50}.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+P_GRID = np.round(np.arange(0.5, 2.0 + 1e-9, 0.1), 1).astype(np.float32)  # 16 values
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    n: int
+    d: int
+    nq: int
+    kind: str               # "mixture" | "sift" | "gist" | "unit"
+    p_mode: str             # "uniform" | "grid"
+    k: int = 10
+    k_choices: tuple = ()
+    ef: int = 64
+    ef_choices: tuple = ()
+    M: int = 16
+    ef_construction: int = 100
+    n_clusters: int = 16
+    traverse_dtype: str = "f32"
+    seed: int = 0
+    grid: float = 0.0       # >0: round base and queries to multiples of `grid`
+    extra: dict = field(default_factory=dict)
+
+    def scaled(self, n: int | None = None, nq: int | None = None, **kw) -> "Workload":
+        """Same recipe at another size (smaller parity cases)."""
+        return replace(self, n=self.n if n is None else n, nq=self.nq if nq is None else nq, **kw)
+
+
+WORKLOADS = {
+    "mixture10k": Workload("mixture10k", 10_000, 32, 100, "mixture", "uniform", k=10, ef=64,
+                           M=16, ef_construction=100, n_clusters=16),
+    "sift1m": Workload("sift1m", 1_000_000, 128, 10_000, "sift", "grid", k=10, ef=64,
+                       ef_choices=(16, 32, 64, 128, 256, 512), M=32, ef_construction=200,
+                       n_clusters=1000),
+    "sift1m_fp16": Workload("sift1m_fp16", 1_000_000, 128, 10_000, "sift", "uniform", k=10, ef=64,
+                            ef_choices=(16, 32, 64, 128, 256, 512), M=32, ef_construction=200,
+                            n_clusters=1000, traverse_dtype="f16"),
+    "gist1m": Workload("gist1m", 1_000_000, 960, 10_000, "gist", "uniform", k=10,
+                       k_choices=(1, 10, 100), ef=128, ef_choices=(32, 64, 128, 256, 512),
+                       M=32, ef_construction=200, n_clusters=100, traverse_dtype="bf16"),
+    "unit10m": Workload("unit10m", 10_000_000, 96, 10_000, "unit", "uniform", k=10,
+                        k_choices=(10, 50), ef=128, M=32, ef_construction=200,
+                        traverse_dtype="f16"),
+}
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.default_rng(seed)
+
+
+def _mixture(rng: np.random.Generator, centres: np.ndarray, n: int, point_std: float) -> np.ndarray:
+    c = rng.integers(0, centres.shape[0], size=n)
+    x = centres[c] + rng.standard_normal((n, centres.shape[1]), dtype=np.float32) * point_std
+    return x.astype(np.float32)
+
+
+def _centres(w: Workload) -> np.ndarray:
+    """Cluster centres, drawn from the base stream's own generator (seed 1000+seed)."""
+    rng = _rng(1000 + w.seed)
+    if w.kind == "mixture":
+        return (rng.standard_normal((w.n_clusters, w.d), dtype=np.float32) * 2.0).astype(np.float32)
+    if w.kind == "sift":
+        return np.clip(rng.exponential(30.0, size=(w.n_clusters, w.d)), 0, 255).astype(np.float32)
+    if w.kind == "gist":
+        return rng.beta(2.0, 5.0, size=(w.n_clusters, w.d)).astype(np.float32)
+    raise ValueError(w.kind)
+
+
+def _draw_points(w: Workload, rng: np.random.Generator, n: int, centres) -> np.ndarray:
+    if w.kind == "mixture":
+        x = _mixture(rng, centres, n, 1.0)
+    elif w.kind == "sift":
+        x = np.empty((n, w.d), dtype=np.float32)
+        step = 65536
+        for s in range(0, n, step):
+            m = min(step, n - s)
+            c = rng.integers(0, centres.shape[0], size=m)
+            v = centres[c] + rng.standard_normal((m, w.d), dtype=np.float32) * 20.0
+            x[s:s + m] = np.rint(np.clip(v, 0.0, 255.0))
+    elif w.kind == "gist":
+        x = np.empty((n, w.d), dtype=np.float32)
+        step = 16384
+        for s in range(0, n, step):
+            m = min(step, n - s)
+            c = rng.integers(0, centres.shape[0], size=m)
+            mu = np.clip(centres[c], 1e-3, 1 - 1e-3)
+            x[s:s + m] = rng.beta(20.0 * mu, 20.0 * (1.0 - mu)).astype(np.float32)
+    elif w.kind == "unit":
+        x = np.empty((n, w.d), dtype=np.float32)
+        step = 1 << 18
+        for s in range(0, n, step):
+            m = min(step, n - s)
+            v = rng.standard_normal((m, w.d), dtype=np.float32)
+            x[s:s + m] = v / np.linalg.norm(v, axis=1, keepdims=True)
+    else:
+        raise ValueError(w.kind)
+    if w.grid > 0:
+        x = (np.rint(x / w.grid) * w.grid).astype(np.float32)
+    return np.ascontiguousarray(x, dtype=np.float32)
+
+
+def base_vectors(w: Workload) -> np.ndarray:
+    """Base set D, float32 [n, d] row-major."""
+    centres = None if w.kind == "unit" else _centres(w)
+    return _draw_points(w, _rng(w.seed), w.n, centres)
+
+
+def query_vectors(w: Workload) -> np.ndarray:
+    """Query vectors, float32 [nq, d], drawn like the base set."""
+    centres = None if w.kind == "unit" else _centres(w)
+    return _draw_points(w, _rng(w.seed + 1), w.nq, centres)
+
+
+def query_params(w: Workload):
+    """Per-query (p float32 [nq], k int32 [nq], ef int32 [nq])."""
+    rng = _rng(w.seed + 2)
+    if w.p_mode == "grid":
+        p = P_GRID[rng.integers(0, len(P_GRID), size=w.nq)]
+    else:
+        # uniform on (0.5, 2]: 2 - 1.5*U with U uniform on [0, 1)
+        p = (2.0 - 1.5 * rng.random(w.nq)).astype(np.float32)
+    if w.k_choices:
+        k = np.asarray(w.k_choices, dtype=np.int32)[rng.integers(0, len(w.k_choices), size=w.nq)]
+    else:
+        k = np.full(w.nq, w.k, dtype=np.int32)
+    if w.ef_choices:
+        ef = np.asarray(w.ef_choices, dtype=np.int32)[rng.integers(0, len(w.ef_choices), size=w.nq)]
+        ef = np.maximum(ef, k).astype(np.int32)
+    else:
+        ef = np.full(w.nq, w.ef, dtype=np.int32)
+    return p.astype(np.float32), k, ef
+
+
+def hnsw_levels(n: int, M: int, seed: int) -> np.ndarray:
+    """Random HNSW layer of each node: floor(-ln(U) / ln(M)), U uniform on (0, 1]."""
+    rng = _rng(seed)
+    u = 1.0 - rng.random(n)              # (0, 1]
+    lv = np.floor(-np.log(u) / math.log(M)).astype(np.int32)
+    return np.minimum(lv, 15).astype(np.int32)
+
+
+def graph_levels(w: Workload, metric: int) -> np.ndarray:
+    """Levels for G1 (metric=1) or G2 (metric=2) of workload `w`."""
+    return hnsw_levels(w.n, w.M, w.seed + (3 if metric == 1 else 4))
+
+
+def random_candidates(n: int, nq: int, t: int, seed: int, missing_frac: float = 0.0) -> np.ndarray:
+    """Candidate id lists [nq, t] int32 drawn without replacement per row;
+    a fraction of trailing slots is set to -1 (absent) when asked."""
+    rng = _rng(seed)
+    out = np.empty((nq, t), dtype=np.int32)
+    for i in range(nq):
+        out[i] = rng.choice(n, size=t, replace=False)
+    if missing_frac > 0:
+        cut = rng.integers(int(t * (1 - missing_frac)), t + 1, size=nq)
+        for i in range(nq):
+            out[i, cut[i]:] = -1
+    return out

@@ -1,0 +1,362 @@
+"""Pins for the CPU oracle (no GPU): closed forms, library routines, hand-
+derived HNSW graphs and invariants that a plausible mistake in the oracle
+(a dropped term, a wrong exponent or sign, a flipped comparison, a
+transposed operand, a wrong tie rule) would break."""
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+from scipy.spatial.distance import cdist
+
+import oracle
+from paper_2605_02030_gb300 import inputs as I
+
+
+def rng(s=0):
+    return np.random.default_rng(s)
+
+
+# ----------------------------------------------------------------- distances
+def test_lp_sum_hand_values():
+    x = np.array([0.0, 0.0], np.float32)
+    q = np.array([1.0, 4.0], np.float32)
+    assert oracle.lp_sum(x, q, 0.5) == 3.0          # 1 + 2
+    assert oracle.lp_sum(x, q, 1.0) == 5.0
+    assert oracle.lp_sum(x, q, 1.5) == 9.0          # 1 + 8
+    assert oracle.lp_sum(x, q, 2.0) == 17.0
+    assert oracle.lp_sum(q, x, 0.5) == 3.0          # symmetric
+    assert oracle.lp_sum(x, x, 0.7) == 0.0          # |0|^p = 0
+    assert oracle.base_dist(x, q, 1) == 5.0
+    assert oracle.base_dist(x, q, 2) == 17.0
+
+
+@pytest.mark.parametrize("p", [0.5, 0.63, 1.0, 1.37, 1.5, 2.0])
+def test_lp_sum_matches_scipy_minkowski(p):
+    r = rng(1)
+    x = r.normal(size=(20, 37)).astype(np.float32)
+    q = r.normal(size=(37,)).astype(np.float32)
+    ref = cdist(x.astype(np.float64), q[None].astype(np.float64), "minkowski", p=p)[:, 0] ** p
+    got = np.array([oracle.lp_sum(xi, q, p) for xi in x])
+    np.testing.assert_allclose(got, ref, rtol=1e-12)
+    l1 = cdist(x.astype(np.float64), q[None].astype(np.float64), "cityblock")[:, 0]
+    l2 = cdist(x.astype(np.float64), q[None].astype(np.float64), "sqeuclidean")[:, 0]
+    np.testing.assert_allclose([oracle.base_dist(xi, q, 1) for xi in x], l1, rtol=1e-12)
+    np.testing.assert_allclose([oracle.base_dist(xi, q, 2) for xi in x], l2, rtol=1e-12)
+
+
+def test_lp_norm_inequalities():
+    """Norm equivalence in finite dimension (Section 3.1): for p < r,
+    ||v||_r <= ||v||_p <= d^(1/p - 1/r) ||v||_r."""
+    r = rng(2)
+    d = 48
+    ps = [0.5, 0.7, 1.0, 1.3, 1.5, 2.0]
+    for _ in range(20):
+        x = r.normal(size=d).astype(np.float32)
+        q = r.normal(size=d).astype(np.float32)
+        norms = [oracle.lp_sum(x, q, p) ** (1 / p) for p in ps]
+        for i in range(len(ps) - 1):
+            p, rr = ps[i], ps[i + 1]
+            assert norms[i] >= norms[i + 1] * (1 - 1e-12)
+            assert norms[i] <= d ** (1 / p - 1 / rr) * norms[i + 1] * (1 + 1e-12)
+
+
+def test_lp_sum_homogeneity_and_translation():
+    r = rng(3)
+    x = r.integers(-8, 8, size=16).astype(np.float32)
+    q = r.integers(-8, 8, size=16).astype(np.float32)
+    for p in (0.5, 0.9, 1.7):
+        s = oracle.lp_sum(x, q, p)
+        assert oracle.lp_sum(4 * x, 4 * q, p) == pytest.approx(4 ** p * s, rel=1e-12)
+        assert oracle.lp_sum(x + 3, q + 3, p) == pytest.approx(s, rel=1e-12)
+
+
+# ----------------------------------------------------------------- O1
+@pytest.mark.parametrize("p", [1.0, 1.25, 1.5, 2.0])
+def test_exact_knn_matches_kdtree(p):
+    """An independent exact k-NN algorithm (k-d tree, Minkowski p >= 1)."""
+    r = rng(4)
+    base = r.normal(size=(600, 6)).astype(np.float32)
+    qs = r.normal(size=(15, 6)).astype(np.float32)
+    ids, S = oracle.exact_knn(base, qs, p, 7)
+    dist, kid = cKDTree(base.astype(np.float64)).query(qs.astype(np.float64), k=7, p=p)
+    np.testing.assert_array_equal(ids, kid)
+    np.testing.assert_allclose(S ** (1 / p), dist, rtol=1e-10)
+
+
+@pytest.mark.parametrize("p", [0.5, 0.55, 0.8])
+def test_exact_knn_fractional_p_bruteforce(p):
+    r = rng(5)
+    base = r.normal(size=(300, 9)).astype(np.float32)
+    qs = r.normal(size=(10, 9)).astype(np.float32)
+    ids, S = oracle.exact_knn(base, qs, p, 5)
+    pf = float(np.float32(p))            # the oracle takes p as the FP32 query value
+    D = cdist(qs.astype(np.float64), base.astype(np.float64), "minkowski", p=pf) ** pf
+    for i in range(len(qs)):
+        order = np.lexsort((np.arange(len(base)), D[i]))[:5]
+        np.testing.assert_array_equal(ids[i], order)
+        np.testing.assert_allclose(S[i], D[i, order], rtol=1e-12)
+
+
+def test_exact_knn_ties_and_padding():
+    base = np.array([[0.0], [1.0], [1.0], [0.0]], np.float32)
+    ids, S = oracle.exact_knn(base, np.zeros((1, 1), np.float32), 1.0, 3)
+    assert ids.tolist() == [[0, 3, 1]]                  # equal S -> ids ascending
+    assert S.tolist() == [[0.0, 0.0, 1.0]]
+    ids, S = oracle.exact_knn(base[:2], np.zeros((1, 1), np.float32), 0.5, 4)
+    assert ids.tolist() == [[0, 1, -1, -1]]
+    assert np.isinf(S[0, 2:]).all()
+
+
+# ----------------------------------------------------------------- O2 (heuristic + build)
+def test_heuristic_line():
+    base = np.array([[0.0], [1.0], [2.0], [3.0]], np.float32)
+    # base point is node 0; candidates 1, 2, 3 at L1 distances 1, 2, 3
+    sel = oracle.select_heuristic(base, [1, 2, 3], [1.0, 2.0, 3.0], 3, metric=1)
+    assert sel.tolist() == [1]
+
+
+def test_heuristic_plane_and_limit():
+    base = np.array([[0, 0], [1, 0], [-1, 0], [0, 1], [2, 0]], np.float32)
+    cand, cd = [1, 2, 3, 4], [1.0, 1.0, 1.0, 4.0]       # squared L2 to node 0
+    assert oracle.select_heuristic(base, cand, cd, 4, metric=2).tolist() == [1, 2, 3]
+    assert oracle.select_heuristic(base, cand, cd, 2, metric=2).tolist() == [1, 2]
+
+
+def test_heuristic_tie_rule():
+    """e equidistant from the base point and a kept neighbour is dropped:
+    a candidate is kept only if strictly nearer to the base point."""
+    base = np.array([[0.0], [2.0], [1.0]], np.float32)   # b=0, r=node1 at 2, e=node2 at 1
+    # candidates sorted by distance to b: node2 (1) first -> kept; then node1 (2):
+    # dist(node1, node2) = 1 < 2 -> dropped
+    assert oracle.select_heuristic(base, [2, 1], [1.0, 2.0], 2, 1).tolist() == [2]
+    # r kept first (closer), then e with dist(e, b) == dist(e, r)
+    base = np.array([[0.0], [1.0], [2.0]], np.float32)   # b=0; r=1 (d 1); e=2 (d 2), dist(e,r)=1
+    assert oracle.select_heuristic(base, [1, 2], [1.0, 2.0], 2, 1).tolist() == [1]
+    base2 = np.array([[0.0, 0.0], [-1.0, 0.0], [1.0, 0.0]], np.float32)
+    # e=(1,0): d(e,b)=1, r=(-1,0): d(e,r)=2 -> kept
+    assert oracle.select_heuristic(base2, [1, 2], [1.0, 1.0], 2, 1).tolist() == [1, 2]
+    base3 = np.array([[0.0, 0.0], [1.0, 0.0], [0.5, 0.5]], np.float32)
+    # L1: r=(1,0) d 1, e=(0.5,0.5) d 1 -> d(e,r) = 1 == d(e,b) -> dropped (strict rule)
+    assert oracle.select_heuristic(base3, [1, 2], [1.0, 1.0], 2, 1).tolist() == [1]
+
+
+def _lists(g, l):
+    lv = g["levels"][l]
+    return {int(v): lv["nbrs"][lv["offsets"][i]:lv["offsets"][i + 1]].tolist()
+            for i, v in enumerate(lv["nodes"])}
+
+
+def test_build_chain_by_hand():
+    """Points 0..5 on a line, one layer, M=2: each insertion links to its
+    left neighbour only (the heuristic drops the others), giving a chain."""
+    base = np.arange(6, dtype=np.float32)[:, None]
+    g = oracle.hnsw_build(base, 1, M=2, ef_construction=10, levels=np.zeros(6, np.int32), M0=4)
+    assert g["num_levels"] == 1 and g["entry_point"] == 0
+    assert _lists(g, 0) == {0: [1], 1: [0, 2], 2: [1, 3], 3: [2, 4], 4: [3, 5], 5: [4]}
+
+
+def test_build_shrink_by_hand():
+    """Node 0 at the origin gets a third link with M0=2 and is pruned by the
+    heuristic over three equidistant neighbours (ties broken by id)."""
+    base = np.array([[0, 0], [4, 0], [-4, 0], [0, 4]], np.float32)
+    g = oracle.hnsw_build(base, 2, M=2, ef_construction=10, levels=np.zeros(4, np.int32), M0=2)
+    assert _lists(g, 0) == {0: [1, 2], 1: [0], 2: [0], 3: [0]}
+
+
+def test_build_levels_by_hand():
+    base = np.arange(4, dtype=np.float32)[:, None]
+    g = oracle.hnsw_build(base, 1, M=2, ef_construction=10, levels=np.array([0, 1, 0, 0], np.int32),
+                          M0=4)
+    assert g["num_levels"] == 2 and g["entry_point"] == 1
+    assert _lists(g, 0) == {0: [1], 1: [0, 2], 2: [1, 3], 3: [2]}
+    assert _lists(g, 1) == {1: []}
+
+
+def _bfs_reach(g, start):
+    lists = g["levels"][0]
+    seen = np.zeros(g["n"], bool)
+    seen[start] = True
+    frontier = [start]
+    while frontier:
+        nxt = []
+        for v in frontier:
+            for u in lists["nbrs"][lists["offsets"][v]:lists["offsets"][v + 1]]:
+                if not seen[u]:
+                    seen[u] = True
+                    nxt.append(int(u))
+        frontier = nxt
+    return seen
+
+
+@pytest.fixture(scope="module")
+def mixture_small():
+    w = I.WORKLOADS["mixture10k"].scaled(n=3000, nq=30)
+    base = I.base_vectors(w)
+    qs = I.query_vectors(w)
+    p, k, ef = I.query_params(w)
+    g1 = oracle.hnsw_build(base, 1, w.M, w.ef_construction, I.graph_levels(w, 1))
+    g2 = oracle.hnsw_build(base, 2, w.M, w.ef_construction, I.graph_levels(w, 2))
+    return w, base, qs, p, g1, g2
+
+
+def test_build_structure(mixture_small):
+    w, base, qs, p, g1, g2 = mixture_small
+    for metric, g in ((1, g1), (2, g2)):
+        levels = I.graph_levels(w, metric)
+        assert g["num_levels"] == levels.max() + 1
+        assert levels[g["entry_point"]] == levels.max()
+        for l, lv in enumerate(g["levels"]):
+            np.testing.assert_array_equal(lv["nodes"], np.nonzero(levels >= l)[0])
+            deg = np.diff(lv["offsets"])
+            assert deg.max() <= (g["max_degree0"] if l == 0 else g["max_degree"])
+            for i, v in enumerate(lv["nodes"]):
+                nb = lv["nbrs"][lv["offsets"][i]:lv["offsets"][i + 1]]
+                assert v not in nb and len(set(nb.tolist())) == len(nb)
+                assert (levels[nb] >= l).all()
+        assert _bfs_reach(g, g["entry_point"]).all()
+
+
+# ----------------------------------------------------------------- O3
+def test_search_full_beam_is_exact(mixture_small):
+    """With ef >= N on a connected layer 0 the beam visits every node, so the
+    first t results are the exact base-metric top-t."""
+    w, base, qs, p, g1, g2 = mixture_small
+    for metric, g, name in ((1, g1, "cityblock"), (2, g2, "sqeuclidean")):
+        D = cdist(qs[:5].astype(np.float64), base.astype(np.float64), name)
+        for i in range(5):
+            ids, dd, nd = oracle.hnsw_search(g, base, qs[i], metric, ef=len(base), t=20)
+            order = np.lexsort((np.arange(len(base)), D[i]))[:20]
+            np.testing.assert_array_equal(ids, order)
+            np.testing.assert_allclose(dd, D[i, order], rtol=1e-12)
+            assert nd >= len(base)
+
+
+def test_search_greedy_chain_by_hand():
+    base = np.arange(6, dtype=np.float32)[:, None]
+    g = oracle.hnsw_build(base, 1, M=2, ef_construction=10, levels=np.zeros(6, np.int32), M0=4)
+    # ef=1 from entry 0 toward 4.2 walks the chain and stops at 4
+    ids, dd, nd = oracle.hnsw_search(g, base, np.array([4.2], np.float32), 1, ef=1, t=1)
+    assert ids.tolist() == [4]
+    assert dd[0] == pytest.approx(0.2, rel=1e-6)
+    ids, dd, nd = oracle.hnsw_search(g, base, np.array([4.2], np.float32), 1, ef=3, t=3)
+    assert ids.tolist() == [4, 5, 3]
+
+
+def test_search_results_sorted_and_recall(mixture_small):
+    w, base, qs, p, g1, g2 = mixture_small
+    D = cdist(qs.astype(np.float64), base.astype(np.float64), "cityblock")
+    hits = 0
+    for i in range(len(qs)):
+        ids, dd, _ = oracle.hnsw_search(g1, base, qs[i], 1, ef=32, t=10)
+        assert (np.diff(dd) >= 0).all()
+        hits += len(set(ids.tolist()) & set(np.argsort(D[i])[:10].tolist()))
+    assert hits / (10 * len(qs)) >= 0.95
+
+
+# ----------------------------------------------------------------- O4
+def test_verify_exact_bruteforce_and_abandon():
+    r = rng(6)
+    base = r.normal(size=(500, 24)).astype(np.float32)
+    q = r.normal(size=24).astype(np.float32)
+    cand = r.choice(500, size=80, replace=False).astype(np.int32)
+    for p in (0.5, 0.77, 1.5, 1.93):
+        pf = float(np.float32(p))
+        S = cdist(q[None].astype(np.float64), base[cand].astype(np.float64), "minkowski", p=pf)[0] ** pf
+        order = np.lexsort((cand, S))[:10]
+        a_ids, a_S, a_terms = oracle.verify_exact(base, q, p, cand, 10, abandon=True)
+        b_ids, b_S, b_terms = oracle.verify_exact(base, q, p, cand, 10, abandon=False)
+        np.testing.assert_array_equal(b_ids, cand[order])
+        np.testing.assert_allclose(b_S, S[order], rtol=1e-12)
+        np.testing.assert_array_equal(a_ids, b_ids)
+        np.testing.assert_array_equal(a_S, b_S)
+        assert b_terms == 80 * 24 and a_terms < b_terms
+
+
+def test_verify_exact_absent_and_short():
+    base = np.arange(5, dtype=np.float32)[:, None]
+    ids, S, _ = oracle.verify_exact(base, np.array([0], np.float32), 1.0, [3, -1, 1], 4)
+    assert ids.tolist() == [1, 3, -1, -1]
+    assert S[:2].tolist() == [1.0, 3.0] and np.isinf(S[2:]).all()
+
+
+def test_verify_paper_worked_example():
+    """K=2, kappa=2, tau=1: S values (p=1, q=0) in candidate order 5,3 | 4,1 | 6,7 | 0.5.
+    R={3,5}; batch {4,1} -> R_new={1,3}, overlap 1/2 < 1; batch {6,7} ->
+    R_new={1,3}, overlap 2/2 >= 1 -> stop before the last candidate."""
+    vals = np.array([5, 3, 4, 1, 6, 7, 0.5], np.float32)
+    base = vals[:, None]
+    cand = np.arange(7, dtype=np.int32)
+    ids, S, nlp, nb = oracle.verify_paper(base, np.zeros(1, np.float32), 1.0, cand, 2, 2, 1.0)
+    assert ids.tolist() == [3, 1] and S.tolist() == [1.0, 3.0]
+    assert nlp == 6 and nb == 2
+    # a threshold above 1 never stops: the last candidate is reached
+    ids, S, nlp, nb = oracle.verify_paper(base, np.zeros(1, np.float32), 1.0, cand, 2, 2, 1.5)
+    assert ids.tolist() == [6, 3] and nlp == 7 and nb == 3
+    # tau <= 0 stops after the first batch
+    ids, S, nlp, nb = oracle.verify_paper(base, np.zeros(1, np.float32), 1.0, cand, 2, 2, 0.0)
+    assert ids.tolist() == [3, 1] and nlp == 4 and nb == 1
+    # ragged last batch (kappa=4 over 5 remaining -> batches of 4 and 1)
+    ids, S, nlp, nb = oracle.verify_paper(base, np.zeros(1, np.float32), 1.0, cand, 2, 4, 1.5)
+    assert ids.tolist() == [6, 3] and nb == 2
+
+
+def test_verify_paper_never_stopping_equals_exact():
+    r = rng(7)
+    base = r.normal(size=(400, 16)).astype(np.float32)
+    q = r.normal(size=16).astype(np.float32)
+    cand = r.choice(400, size=64, replace=False).astype(np.int32)
+    for p in (0.6, 1.2, 1.8):
+        a, Sa, _, _ = oracle.verify_paper(base, q, p, cand, 10, 10, 1.01)
+        b, Sb, _ = oracle.verify_exact(base, q, p, cand, 10)
+        np.testing.assert_array_equal(a, b)
+        np.testing.assert_array_equal(Sa, Sb)
+
+
+# ----------------------------------------------------------------- Algorithm 1
+def test_uhnsw_full_candidate_set_equals_exact(mixture_small):
+    """t = ef = N: C is every point, so both verification modes (tau > 1)
+    return the exact L_p top-K of O1."""
+    w, base, qs, p, g1, g2 = mixture_small
+    n = len(base)
+    ids_e, S_e = oracle.exact_knn(base, qs[:6], p[:6], 10)
+    for mode in (0, 1):
+        ids, dist, st = oracle.uhnsw_batch(g1, g2, base, qs[:6], p[:6], 10, n, t=n, tau=1.5,
+                                           mode=mode)
+        np.testing.assert_array_equal(ids, ids_e)
+        np.testing.assert_allclose(dist, S_e ** (1 / p[:6, None].astype(np.float64)), rtol=1e-12)
+
+
+def test_uhnsw_direct_p1_p2(mixture_small):
+    w, base, qs, p, g1, g2 = mixture_small
+    n = len(base)
+    D1 = cdist(qs[:3].astype(np.float64), base.astype(np.float64), "cityblock")
+    D2 = cdist(qs[:3].astype(np.float64), base.astype(np.float64), "euclidean")
+    for pp, D in ((1.0, D1), (2.0, D2)):
+        ids, dist, st = oracle.uhnsw_batch(g1, g2, base, qs[:3], pp, 10, n)
+        for i in range(3):
+            order = np.lexsort((np.arange(n), D[i]))[:10]
+            np.testing.assert_array_equal(ids[i], order)
+            np.testing.assert_allclose(dist[i], D[i, order], rtol=1e-12)
+        assert (st[:, 1] == 0).all()      # no L_p verification
+
+
+def test_uhnsw_routing_cutoff(mixture_small):
+    """p <= 1.4 searches G1, p > 1.4 searches G2: a G2 whose entry point has no
+    links returns only that entry point."""
+    w, base, qs, p, g1, g2 = mixture_small
+    n = len(base)
+    dead = {"num_levels": 1, "entry_point": 7, "max_degree0": 2, "max_degree": 2, "n": n,
+            "levels": [{"nodes": np.arange(n, dtype=np.int32),
+                        "offsets": np.zeros(n + 1, np.int64), "nbrs": np.zeros(0, np.int32)}]}
+    ids_lo, _, _ = oracle.uhnsw_query(g1, dead, base, qs[0], np.float32(1.4), 5, 32)
+    ids_hi, _, _ = oracle.uhnsw_query(g1, dead, base, qs[0], np.nextafter(np.float32(1.4),
+                                                                          np.float32(2)), 5, 32)
+    assert (ids_lo >= 0).all()
+    assert ids_hi.tolist() == [7, -1, -1, -1, -1]
+    # a custom cutoff moves the boundary
+    ids_c, _, _ = oracle.uhnsw_query(g1, dead, base, qs[0], np.float32(0.7), 5, 32, cutoff=0.6)
+    assert ids_c.tolist() == [7, -1, -1, -1, -1]
+
+
+def test_recall_definition():
+    assert oracle.recall([[1, 2, 3]], [[3, 4, 1]]) == pytest.approx(2 / 3)
+    assert oracle.recall([[1, 2], [5, 6]], [[1, 2], [6, 7]]) == pytest.approx(0.75)
