@@ -1,0 +1,248 @@
+/*
+ * uhnsw.h: C ABI of the GB300 U-HNSW query path.
+ *
+ * U-HNSW (arxiv 2605.02030) answers a query (q, p) with the K nearest base
+ * vectors under that query's own L_p distance, 0.5 <= p <= 2 (Sections 1.1
+ * and 2.1), from two HNSW graphs: G1 built under L1 and G2 built under L2
+ * (Section 3.1).  A query with p <= cutoff (1.4 by default) searches G1,
+ * otherwise G2 ("Candidate generation", Algorithm 1 lines 1-5); the t nearest
+ * under the base metric form the candidate set C, which is re-ranked under
+ * L_p ("Candidate verification", Algorithm 1 lines 6-10).  p == 1 and p == 2
+ * search G1 / G2 for the K nearest directly, without verification (Section 3,
+ * introduction).
+ *
+ * Conventions for every entry point:
+ *   - Return value: UHNSW_OK (0) or a negative UHNSW_E* code; nothing throws
+ *     across the ABI.  uhnsw_last_error() returns a message for the calling
+ *     thread's last failure.
+ *   - Arguments are validated before any work is queued; on failure nothing
+ *     is written.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     device memory of the current device (e.g. torch tensors' data_ptr()).
+ *     All inputs stay owned by the caller.  uhnsw_load copies what it needs.
+ *   - Device work is queued on the caller's stream (a cudaStream_t passed as
+ *     void*, NULL = legacy default stream); results are valid once that
+ *     stream has synchronised.  Calls on one index may be queued on several
+ *     streams concurrently unless stated otherwise.
+ *   - Order of results: ascending by (distance, id).  Missing results are
+ *     padded with id -1 and distance +inf.
+ *   - Every device wait inside the library is bounded; a wait that gives up
+ *     records UHNSW_ETIMEOUT in the query's status (never traps).
+ */
+#ifndef UHNSW_H_
+#define UHNSW_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define UHNSW_MAX_LEVELS 16
+#define UHNSW_MAX_EF 512   /* largest beam ef' = max(ef, t, k) */
+#define UHNSW_MAX_DIM 2048
+#define UHNSW_MAX_DEGREE 128
+
+#define UHNSW_OK 0
+#define UHNSW_EINVAL (-1)    /* bad argument or malformed graph */
+#define UHNSW_EOOM (-2)      /* device or host allocation failed */
+#define UHNSW_ECUDA (-3)     /* a CUDA runtime call failed (no device, ...) */
+#define UHNSW_ETIMEOUT (-4)  /* a bounded device wait gave up */
+#define UHNSW_ECAPACITY (-5) /* a size above a documented limit */
+
+typedef enum { UHNSW_F32 = 0, UHNSW_F16 = 1, UHNSW_BF16 = 2 } uhnsw_dtype;
+
+typedef enum {
+  UHNSW_VERIFY_EXACT = 0, /* top-K by L_p over all of C, with partial-sum abandon */
+  UHNSW_VERIFY_PAPER = 1  /* Algorithm 1 lines 6-10: batches of kappa, stop at tau */
+} uhnsw_verify_mode;
+
+typedef struct uhnsw_index uhnsw_index;
+
+/*
+ * One HNSW graph in CSR form per level (Section 2.2: a multi-layer proximity
+ * graph).  All arrays are HOST memory owned by the caller and only read
+ * during uhnsw_load.  Level l lists the nodes present at that level as sorted
+ * global ids level_nodes[l][0..level_count[l]) (level 0 may pass NULL, meaning
+ * all n nodes in id order), their adjacency rows
+ * level_nbrs[l][level_offsets[l][i] .. level_offsets[l][i+1]) as global ids,
+ * with at most max_degree0 links at level 0 and max_degree above.  Every node
+ * of level l > 0 must also be present at level l-1; entry_point must be a
+ * node of the top level num_levels-1.
+ */
+typedef struct {
+  int32_t num_levels;
+  int32_t entry_point;
+  int32_t max_degree0;
+  int32_t max_degree;
+  const int32_t* level_count;
+  const int32_t* level_nodes[UHNSW_MAX_LEVELS];
+  const int64_t* level_offsets[UHNSW_MAX_LEVELS];
+  const int32_t* level_nbrs[UHNSW_MAX_LEVELS];
+} uhnsw_graph;
+
+typedef struct {
+  /* storage of the copy the beam search reads (the FP32 master copy is kept
+   * for verification and returned distances either way) */
+  uhnsw_dtype traverse_dtype;
+  int32_t reserved[7];
+} uhnsw_load_opts;
+
+/* per-query counters written when uhnsw_search_opts.stats is set */
+enum {
+  UHNSW_STAT_NB = 0,        /* base-metric distance evaluations (N_b of Eq. 1) */
+  UHNSW_STAT_NP = 1,        /* candidates whose L_p sum was started (N_p of Eq. 1) */
+  UHNSW_STAT_TERMS = 2,     /* |x_j - q_j|^p terms accumulated */
+  UHNSW_STAT_EXPANSIONS = 3,/* beam entries expanded at layer 0 */
+  UHNSW_STAT_RESETS = 4,    /* visited-table resets */
+  UHNSW_STAT_STATUS = 5,    /* 0 or a negative UHNSW_E* code for this query */
+  UHNSW_STAT_GRAPH = 6,     /* 1 = G1 (L1), 2 = G2 (L2) */
+  UHNSW_STAT_ADJ = 7,       /* adjacency rows read (upper levels and layer 0) */
+  UHNSW_NSTATS = 8
+};
+
+typedef struct {
+  int32_t t;             /* |C|, candidates verified; 0 => ef (the whole beam); raised to k */
+  int32_t kappa;         /* batch size of Algorithm 1; 0 => k */
+  float tau;             /* early-termination threshold of Algorithm 1; 0 => 0.92 */
+  float cutoff;          /* routing: p <= cutoff searches G1; 0 => 1.4 */
+  int32_t verify_mode;   /* uhnsw_verify_mode */
+  int32_t search_width;  /* beam entries expanded per step; <= 1 => exactly HNSW's order */
+  int32_t persistent;    /* 1: one persistent launch pulling queries from a device queue */
+  int32_t use_graph;     /* 1: capture the launch sequence once per call shape, then replay */
+  int32_t ef_max;        /* bound on ef' over the batch when per-query ef is given; 0 => 512 */
+  int32_t block_threads; /* threads per query block (64, 128 or 256); 0 => autotuned */
+  int32_t* stats;        /* device [nq][UHNSW_NSTATS] int32, or NULL */
+  int32_t reserved[4];
+} uhnsw_search_opts;
+
+/*
+ * Upload an index: base vectors plus G1 (L1) and G2 (L2).
+ *   base      host, n x d float32 row-major; copied to an FP32 master copy and,
+ *             if opts->traverse_dtype != UHNSW_F32, a rounded FP16/BF16 copy.
+ *             Rows are zero-padded on the device to a multiple of 8 elements.
+ *   g1, g2    host CSR graphs over the same n nodes (either may be NULL: a
+ *             query routed to a missing graph fails with UHNSW_EINVAL status).
+ *   opts      may be NULL (FP32 traversal).
+ *   out       receives the index handle; free it with uhnsw_free.
+ * Layer 0 of each graph is stored as a padded [n][max_degree0] table, upper
+ * levels as [rows][max_degree] tables.  Uses the current CUDA device.
+ * Errors: EINVAL (d or n out of range, malformed CSR), EOOM, ECUDA.
+ */
+int uhnsw_load(const float* base, int64_t n, int32_t d, const uhnsw_graph* g1,
+               const uhnsw_graph* g2, const uhnsw_load_opts* opts, uhnsw_index** out);
+
+/*
+ * Algorithm 1 for a batch of nq queries.
+ *   q          device, nq x d float32 row-major
+ *   p          device [nq] float32, each in (0, 2]
+ *   k          device [nq] int32 in [1, k_max], or NULL (all k_max)
+ *   ef         device [nq] int32 >= 1, or NULL (all ef_default)
+ *   k_max      row stride of the outputs, 1 <= k_max <= UHNSW_MAX_EF
+ *   out_ids    device, nq x k_max int64
+ *   out_dist   device, nq x k_max float32 (L_p distance S^(1/p))
+ *   opts       may be NULL (defaults above)
+ * The beam of a query holds ef' = max(ef, t', k) entries, t' = max(t or ef, k)
+ * for general p, t' = k for p in {1, 2}; ef' above the launch bound
+ * (opts->ef_max, or ef_default) or UHNSW_MAX_EF, an invalid p or k, fails that
+ * query alone (status EINVAL in stats, outputs padded).
+ * Errors: EINVAL (host-checkable arguments), ECUDA.
+ */
+int uhnsw_search(uhnsw_index* idx, const float* q, const float* p, const int32_t* k,
+                 const int32_t* ef, int64_t nq, int32_t k_max, int32_t ef_default,
+                 const uhnsw_search_opts* opts, int64_t* out_ids, float* out_dist,
+                 void* stream);
+
+/*
+ * uhnsw_search with HOST arrays: q (nq x d), p, k, ef (or NULL) and the outputs
+ * are host memory (pinned memory makes the copies asynchronous).  The call
+ * copies the inputs to device staging buffers owned by the index, runs the
+ * search on `stream` and copies the results back; it returns after the
+ * stream has synchronised.  Not safe to run concurrently on one index.
+ */
+int uhnsw_search_host(uhnsw_index* idx, const float* q, const float* p, const int32_t* k,
+                      const int32_t* ef, int64_t nq, int32_t k_max, int32_t ef_default,
+                      const uhnsw_search_opts* opts, int64_t* out_ids, float* out_dist,
+                      void* stream);
+
+/*
+ * Candidate verification alone (Algorithm 1 lines 6-10, or the exact mode) on
+ * caller-given candidate sets, for testing the re-ranking step in isolation.
+ *   q      device nq x d float32;  p device [nq] float32 in (0, 2]
+ *   cand   device nq x t int32 base ids in C's order (-1 = absent slot; no
+ *          duplicates within a row)
+ *   k      results per query, 1 <= k <= UHNSW_MAX_EF
+ *   opts   uses verify_mode, kappa, tau and stats (NP / TERMS / STATUS); may be NULL
+ *   out_ids / out_dist   device nq x k int64 / float32
+ * Errors: EINVAL, ECUDA.
+ */
+int uhnsw_verify(uhnsw_index* idx, const float* q, const float* p, const int32_t* cand, int32_t t,
+                 int32_t k, int64_t nq, const uhnsw_search_opts* opts, int64_t* out_ids,
+                 float* out_dist, void* stream);
+
+/*
+ * Exhaustive L_p k-NN over all n base vectors of the FP32 master copy (the
+ * exact answer the recall of Section 4.1.2 is measured against), computed on
+ * the GPU.
+ *   q device nq x d float32; p device [nq]; k in [1, 256];
+ *   out_ids / out_dist device nq x k.
+ * Uses a device workspace owned by the index (grown on demand, freed by
+ * uhnsw_free); not safe to run concurrently on one index.
+ * Errors: EINVAL, EOOM, ECUDA.
+ */
+int uhnsw_exact(uhnsw_index* idx, const float* q, const float* p, int64_t nq, int32_t k,
+                int64_t* out_ids, float* out_dist, void* stream);
+
+/*
+ * Index facts: n, d, padded row length, bytes held on the device, and the
+ * device pointers of the layer-0 tables (for diagnostics).  Any out pointer
+ * may be NULL.
+ */
+int uhnsw_index_info(const uhnsw_index* idx, int64_t* n, int32_t* d, int32_t* d_pad,
+                     int64_t* device_bytes, int32_t* max_degree0);
+
+/* Reads and clears the index's sticky device error word (synchronises the
+ * device).  Returns UHNSW_OK or the first recorded code. */
+int uhnsw_device_status(uhnsw_index* idx);
+
+/* Frees every device and host allocation of the index (NULL is a no-op). */
+void uhnsw_free(uhnsw_index* idx);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* uhnsw_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Index construction (Section 2.2, the HNSW insertion the paper builds G1 and
+ * G2 with): host-side and multi-threaded; not part of the query path.
+ * ---------------------------------------------------------------------- */
+
+typedef struct uhnsw_built uhnsw_built;
+
+/*
+ * Build one HNSW graph on the host.
+ *   base      host n x d float32 row-major (read during the call only)
+ *   metric    1 = L1 (G1), 2 = squared L2 (G2)
+ *   M         links per inserted node; layer-0 lists hold up to 2M
+ *   ef_construction   beam width of the insertion search
+ *   levels    host [n] int32, the level of each node (drawn by the caller)
+ *   threads   worker threads (<= 0: all hardware threads); with 1 thread the
+ *             insertion order, and so the graph, is deterministic
+ *   out       receives the graph; read it with uhnsw_built_graph, free it with
+ *             uhnsw_built_free
+ * Errors: EINVAL, EOOM.
+ */
+int uhnsw_build_graph(const float* base, int64_t n, int32_t d, int32_t metric, int32_t M,
+                      int32_t ef_construction, const int32_t* levels, int32_t threads,
+                      uhnsw_built** out);
+
+/* Fills `view` with host pointers into the built graph (valid until
+ * uhnsw_built_free); level 0 lists every node, so level_nodes[0] is NULL. */
+int uhnsw_built_graph(const uhnsw_built* b, uhnsw_graph* view);
+
+void uhnsw_built_free(uhnsw_built* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UHNSW_H_ */

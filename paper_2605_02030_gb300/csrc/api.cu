@@ -1,0 +1,638 @@
+// Host side of the C ABI declared in uhnsw.h: argument validation, index
+// upload (FP32 master rows, FP16/BF16 traversal rows, padded layer-0 link
+// tables, upper-level link rows), kernel dispatch, CUDA-graph replay of
+// repeated call shapes, the host-buffer search and the error channel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "launch.h"
+#include "uhnsw.h"
+#include "uhnsw_internal.h"
+
+namespace uhnsw_internal {
+
+static thread_local char g_err[512] = {0};
+
+void clear_error() { g_err[0] = 0; }
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+}  // namespace uhnsw_internal
+
+using uhnsw_internal::clear_error;
+using uhnsw_internal::fail;
+using namespace uhnsw_dev;
+
+namespace {
+
+struct DevGraph {
+  bool present = false;
+  int32_t* ell0 = nullptr;
+  int32_t* up_row = nullptr;
+  int32_t* up_adj = nullptr;
+  int32_t entry = 0, top_level = 0, deg0 = 0, deg = 0;
+  int64_t bytes = 0;
+};
+
+struct GraphKey {
+  const void* ptr[7];
+  int64_t nq;
+  int32_t k_max, ef_default;
+  uhnsw_search_opts opts;
+  void* stream;
+  bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(*this)) == 0; }
+};
+
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec;
+};
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? UHNSW_EOOM : UHNSW_ECUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+int next_pow2_bits(int64_t x) {
+  int b = 0;
+  while ((1ll << b) < x) ++b;
+  return b;
+}
+
+}  // namespace
+
+struct uhnsw_index {
+  int device = 0;
+  int num_sms = 0;
+  int64_t n = 0;
+  int32_t d = 0, d_pad = 0;
+  uhnsw_dtype tdtype = UHNSW_F32;
+  float* base32 = nullptr;
+  void* trav = nullptr;
+  DevGraph g[2];
+  int32_t* err = nullptr;         // sticky device error word
+  int32_t* queue_head = nullptr;  // persistent-launch work counter
+  int64_t bytes = 0;
+  cudaStream_t capture_stream = nullptr;
+  std::mutex mu;
+  std::vector<GraphEntry> graphs;
+  // host-buffer search staging
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  // exact-search workspace
+  void* exact_ws = nullptr;
+  size_t exact_ws_bytes = 0;
+
+  ~uhnsw_index() {
+    for (auto& e : graphs) cudaGraphExecDestroy(e.exec);
+    for (auto& gg : g) {
+      cudaFree(gg.ell0);
+      cudaFree(gg.up_row);
+      cudaFree(gg.up_adj);
+    }
+    if (trav && trav != base32) cudaFree(trav);
+    cudaFree(base32);
+    cudaFree(err);
+    cudaFree(queue_head);
+    cudaFree(stage);
+    cudaFree(exact_ws);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+  }
+};
+
+namespace {
+
+// Checks the CSR of one graph and builds its device tables on the host.
+int check_and_pack(const uhnsw_graph* g, int64_t n, const char* name, std::vector<int32_t>& ell0,
+                   std::vector<int32_t>& up_row, std::vector<int32_t>& up_adj) {
+  if (g->num_levels < 1 || g->num_levels > UHNSW_MAX_LEVELS)
+    return fail(UHNSW_EINVAL, "%s: num_levels %d not in [1, %d]", name, g->num_levels,
+                UHNSW_MAX_LEVELS);
+  if (!g->level_count) return fail(UHNSW_EINVAL, "%s: level_count is NULL", name);
+  const int32_t deg0 = g->max_degree0, deg = g->max_degree;
+  if (deg0 < 1 || deg0 > UHNSW_MAX_DEGREE || deg < 1 || deg > UHNSW_MAX_DEGREE)
+    return fail(UHNSW_EINVAL, "%s: degrees (%d, %d) not in [1, %d]", name, deg0, deg,
+                UHNSW_MAX_DEGREE);
+  if (g->level_count[0] != n)
+    return fail(UHNSW_EINVAL, "%s: level 0 has %d nodes, base has %lld", name, g->level_count[0],
+                (long long)n);
+  std::vector<int8_t> top(n, 0);  // highest level of each node
+  for (int32_t l = 0; l < g->num_levels; ++l) {
+    const int64_t cnt = g->level_count[l];
+    const int32_t* nodes = g->level_nodes[l];
+    const int64_t* off = g->level_offsets[l];
+    const int32_t* nb = g->level_nbrs[l];
+    if (cnt < 1 || cnt > n) return fail(UHNSW_EINVAL, "%s: level %d has %lld nodes", name, l, (long long)cnt);
+    if (!off || (!nb && off[cnt] > 0)) return fail(UHNSW_EINVAL, "%s: level %d arrays missing", name, l);
+    if (l > 0 && !nodes) return fail(UHNSW_EINVAL, "%s: level %d nodes is NULL", name, l);
+    if (off[0] != 0) return fail(UHNSW_EINVAL, "%s: level %d offsets[0] != 0", name, l);
+    const int32_t cap = l == 0 ? deg0 : deg;
+    for (int64_t i = 0; i < cnt; ++i) {
+      const int32_t v = nodes ? nodes[i] : (int32_t)i;
+      if (v < 0 || v >= n) return fail(UHNSW_EINVAL, "%s: level %d node %d out of range", name, l, v);
+      if (nodes && i > 0 && nodes[i - 1] >= v)
+        return fail(UHNSW_EINVAL, "%s: level %d nodes not strictly ascending", name, l);
+      if (l > 0 && top[v] != l - 1)
+        return fail(UHNSW_EINVAL, "%s: node %d on level %d but not on level %d", name, v, l, l - 1);
+      const int64_t a = off[i], b = off[i + 1];
+      if (b < a || b - a > cap)
+        return fail(UHNSW_EINVAL, "%s: level %d node %d has degree %lld (cap %d)", name, l, v,
+                    (long long)(b - a), cap);
+      for (int64_t e = a; e < b; ++e)
+        if (nb[e] < 0 || nb[e] >= n)
+          return fail(UHNSW_EINVAL, "%s: level %d link %d out of range", name, l, nb[e]);
+      if (l > 0) top[v] = (int8_t)l;
+    }
+  }
+  // every neighbour at level l must itself be on level l
+  for (int32_t l = 1; l < g->num_levels; ++l) {
+    const int64_t cnt = g->level_count[l];
+    for (int64_t e = 0; e < g->level_offsets[l][cnt]; ++e)
+      if (top[g->level_nbrs[l][e]] < l)
+        return fail(UHNSW_EINVAL, "%s: level %d links to node %d, which is not on it", name, l,
+                    g->level_nbrs[l][e]);
+  }
+  if (g->entry_point < 0 || g->entry_point >= n || top[g->entry_point] != g->num_levels - 1)
+    return fail(UHNSW_EINVAL, "%s: entry point %d is not on the top level", name, g->entry_point);
+
+  ell0.assign(n * (int64_t)deg0, -1);
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t a = g->level_offsets[0][i], b = g->level_offsets[0][i + 1];
+    const int32_t v = g->level_nodes[0] ? g->level_nodes[0][i] : (int32_t)i;
+    std::copy(g->level_nbrs[0] + a, g->level_nbrs[0] + b, ell0.begin() + (int64_t)v * deg0);
+  }
+  up_row.assign(n, -1);
+  int64_t rows = 0;
+  for (int64_t v = 0; v < n; ++v)
+    if (top[v] > 0) {
+      up_row[v] = (int32_t)rows;
+      rows += top[v];
+    }
+  if (rows > INT32_MAX) return fail(UHNSW_ECAPACITY, "%s: too many upper-level rows", name);
+  up_adj.assign(std::max<int64_t>(rows, 1) * deg, -1);
+  for (int32_t l = 1; l < g->num_levels; ++l)
+    for (int64_t i = 0; i < g->level_count[l]; ++i) {
+      const int32_t v = g->level_nodes[l][i];
+      const int64_t a = g->level_offsets[l][i], b = g->level_offsets[l][i + 1];
+      std::copy(g->level_nbrs[l] + a, g->level_nbrs[l] + b,
+                up_adj.begin() + ((int64_t)up_row[v] + l - 1) * deg);
+    }
+  return UHNSW_OK;
+}
+
+template <typename T>
+int upload(const std::vector<T>& h, T** d, int64_t* bytes) {
+  const size_t sz = h.size() * sizeof(T);
+  cudaError_t e = cudaMalloc(d, sz);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  *bytes += sz;
+  e = cudaMemcpy(*d, h.data(), sz, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+  return UHNSW_OK;
+}
+
+GraphDev to_dev(const DevGraph& g) {
+  GraphDev r;
+  r.ell0 = g.present ? g.ell0 : nullptr;
+  r.up_row = g.up_row;
+  r.up_adj = g.up_adj;
+  r.entry = g.entry;
+  r.top_level = g.top_level;
+  r.deg0 = g.deg0;
+  r.deg = g.deg;
+  return r;
+}
+
+constexpr int kBlock = 128;
+
+}  // namespace
+
+extern "C" const char* uhnsw_last_error(void) { return uhnsw_internal::g_err; }
+
+extern "C" int uhnsw_load(const float* base, int64_t n, int32_t d, const uhnsw_graph* g1,
+                          const uhnsw_graph* g2, const uhnsw_load_opts* opts, uhnsw_index** out) {
+  clear_error();
+  if (!out) return fail(UHNSW_EINVAL, "uhnsw_load: out is NULL");
+  *out = nullptr;
+  if (!base) return fail(UHNSW_EINVAL, "uhnsw_load: base is NULL");
+  if (n < 1 || n > INT32_MAX) return fail(UHNSW_EINVAL, "uhnsw_load: n=%lld out of range", (long long)n);
+  if (d < 1 || d > UHNSW_MAX_DIM) return fail(UHNSW_EINVAL, "uhnsw_load: d=%d out of range", d);
+  if (!g1 && !g2) return fail(UHNSW_EINVAL, "uhnsw_load: no graph given");
+  const uhnsw_dtype dt = opts ? opts->traverse_dtype : UHNSW_F32;
+  if (dt != UHNSW_F32 && dt != UHNSW_F16 && dt != UHNSW_BF16)
+    return fail(UHNSW_EINVAL, "uhnsw_load: unknown traverse dtype %d", (int)dt);
+
+  std::vector<int32_t> ell[2], upr[2], upa[2];
+  try {
+    const uhnsw_graph* gs[2] = {g1, g2};
+    for (int i = 0; i < 2; ++i) {
+      if (!gs[i]) continue;
+      int rc = check_and_pack(gs[i], n, i == 0 ? "G1" : "G2", ell[i], upr[i], upa[i]);
+      if (rc != UHNSW_OK) return rc;
+    }
+  } catch (const std::bad_alloc&) {
+    return fail(UHNSW_EOOM, "uhnsw_load: out of host memory");
+  }
+
+  uhnsw_index* idx = new (std::nothrow) uhnsw_index();
+  if (!idx) return fail(UHNSW_EOOM, "uhnsw_load: out of host memory");
+  cudaError_t e = cudaGetDevice(&idx->device);
+  if (e != cudaSuccess) {
+    delete idx;
+    return cuda_fail(e, "uhnsw_load: cudaGetDevice");
+  }
+  e = cudaDeviceGetAttribute(&idx->num_sms, cudaDevAttrMultiProcessorCount, idx->device);
+  if (e != cudaSuccess) {
+    delete idx;
+    return cuda_fail(e, "uhnsw_load: cudaDeviceGetAttribute");
+  }
+  idx->n = n;
+  idx->d = d;
+  idx->d_pad = (d + 7) / 8 * 8;
+  idx->tdtype = dt;
+  int rc = UHNSW_OK;
+  const size_t row32 = (size_t)idx->d_pad * 4;
+  do {
+    e = cudaMalloc(&idx->base32, row32 * n);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "uhnsw_load: base"); break; }
+    idx->bytes += row32 * n;
+    e = cudaMemset(idx->base32, 0, row32 * n);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2D(idx->base32, row32, base, (size_t)d * 4, (size_t)d * 4, n,
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "uhnsw_load: base upload"); break; }
+    if (dt == UHNSW_F32) {
+      idx->trav = idx->base32;
+    } else {
+      e = cudaMalloc(&idx->trav, row32 / 2 * n);
+      if (e != cudaSuccess) { rc = cuda_fail(e, "uhnsw_load: traversal copy"); break; }
+      idx->bytes += row32 / 2 * n;
+      e = launch_convert(idx->base32, idx->trav, dt, (int64_t)idx->d_pad * n, 0);
+      if (e == cudaSuccess) e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) { rc = cuda_fail(e, "uhnsw_load: convert"); break; }
+    }
+    const uhnsw_graph* gs[2] = {g1, g2};
+    for (int i = 0; i < 2 && rc == UHNSW_OK; ++i) {
+      if (!gs[i]) continue;
+      DevGraph& G = idx->g[i];
+      G.present = true;
+      G.entry = gs[i]->entry_point;
+      G.top_level = gs[i]->num_levels - 1;
+      G.deg0 = gs[i]->max_degree0;
+      G.deg = gs[i]->max_degree;
+      rc = upload(ell[i], &G.ell0, &idx->bytes);
+      if (rc == UHNSW_OK) rc = upload(upr[i], &G.up_row, &idx->bytes);
+      if (rc == UHNSW_OK) rc = upload(upa[i], &G.up_adj, &idx->bytes);
+    }
+    if (rc != UHNSW_OK) break;
+    e = cudaMalloc(&idx->err, 4);
+    if (e == cudaSuccess) e = cudaMalloc(&idx->queue_head, 64);
+    if (e == cudaSuccess) e = cudaMemset(idx->err, 0, 4);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&idx->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "uhnsw_load: state"); break; }
+  } while (0);
+  if (rc != UHNSW_OK) {
+    delete idx;
+    return rc;
+  }
+  *out = idx;
+  return UHNSW_OK;
+}
+
+namespace {
+
+struct Prepared {
+  QueryArgs a;
+  TeamShape shape;
+  size_t smem;
+  int grid;
+  bool persistent;
+};
+
+// Validates host-side search arguments and fills the launch description.
+int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32_t* k,
+                   const int32_t* ef, int64_t nq, int32_t k_max, int32_t ef_default,
+                   const uhnsw_search_opts* o, int64_t* out_ids, float* out_dist, Prepared* P) {
+  if (!idx) return fail(UHNSW_EINVAL, "uhnsw_search: index is NULL");
+  if (nq < 0 || nq > INT32_MAX) return fail(UHNSW_EINVAL, "uhnsw_search: nq=%lld", (long long)nq);
+  if (nq > 0 && (!q || !p || !out_ids || !out_dist))
+    return fail(UHNSW_EINVAL, "uhnsw_search: NULL q/p/out pointer");
+  if (k_max < 1 || k_max > UHNSW_MAX_EF)
+    return fail(UHNSW_EINVAL, "uhnsw_search: k_max=%d not in [1, %d]", k_max, UHNSW_MAX_EF);
+  if (ef_default < 1 || ef_default > UHNSW_MAX_EF)
+    return fail(UHNSW_EINVAL, "uhnsw_search: ef_default=%d not in [1, %d]", ef_default, UHNSW_MAX_EF);
+  uhnsw_search_opts opts;
+  std::memset(&opts, 0, sizeof(opts));
+  if (o) opts = *o;
+  if (opts.t < 0 || opts.t > UHNSW_MAX_EF) return fail(UHNSW_EINVAL, "uhnsw_search: t=%d", opts.t);
+  if (opts.kappa < 0) return fail(UHNSW_EINVAL, "uhnsw_search: kappa=%d", opts.kappa);
+  if (!(opts.tau >= 0.f) || !std::isfinite(opts.tau)) return fail(UHNSW_EINVAL, "uhnsw_search: tau");
+  if (!(opts.cutoff >= 0.f) || !std::isfinite(opts.cutoff))
+    return fail(UHNSW_EINVAL, "uhnsw_search: cutoff");
+  if (opts.verify_mode != UHNSW_VERIFY_EXACT && opts.verify_mode != UHNSW_VERIFY_PAPER)
+    return fail(UHNSW_EINVAL, "uhnsw_search: verify_mode=%d", opts.verify_mode);
+  if (opts.search_width < 0 || opts.search_width > 8)
+    return fail(UHNSW_EINVAL, "uhnsw_search: search_width=%d not in [0, 8]", opts.search_width);
+  if (opts.block_threads != 0 && opts.block_threads != kBlock)
+    return fail(UHNSW_EINVAL, "uhnsw_search: block_threads=%d unsupported", opts.block_threads);
+  if (opts.ef_max < 0 || opts.ef_max > UHNSW_MAX_EF)
+    return fail(UHNSW_EINVAL, "uhnsw_search: ef_max=%d", opts.ef_max);
+
+  int ef_cap;
+  if (ef) ef_cap = opts.ef_max > 0 ? opts.ef_max : UHNSW_MAX_EF;
+  else ef_cap = std::max({ef_default, opts.t, k_max});
+  if (ef_cap > UHNSW_MAX_EF)
+    return fail(UHNSW_EINVAL, "uhnsw_search: beam %d exceeds %d", ef_cap, UHNSW_MAX_EF);
+  const int width = std::max(1, opts.search_width);
+  int deg0 = 0, deg = 0;
+  for (auto& G : idx->g)
+    if (G.present) {
+      deg0 = std::max(deg0, G.deg0);
+      deg = std::max(deg, G.deg);
+    }
+  const int cmax = std::max({width * deg0, deg, kBlock / 8});
+  int hb = next_pow2_bits(4ll * (ef_cap + width * deg0));
+  hb = std::max(hb, 9);
+  if (hb > 15) return fail(UHNSW_ECAPACITY, "uhnsw_search: visited table too large");
+  const SmemLayout L(idx->d_pad, ef_cap, hb, cmax, k_max, 0);
+  TeamShape sh;
+  if (!pick_shape(idx->tdtype, idx->d_pad / (idx->tdtype == UHNSW_F32 ? 4 : 8), &sh))
+    return fail(UHNSW_ECAPACITY, "uhnsw_search: no kernel shape for d=%d", idx->d);
+
+  QueryArgs& a = P->a;
+  std::memset(&a, 0, sizeof(a));
+  a.base32 = idx->base32;
+  a.trav = idx->trav;
+  a.n = idx->n;
+  a.d = idx->d;
+  a.d_pad = idx->d_pad;
+  a.g[0] = to_dev(idx->g[0]);
+  a.g[1] = to_dev(idx->g[1]);
+  a.q = q;
+  a.p = p;
+  a.k = k;
+  a.ef = ef;
+  a.nq = nq;
+  a.k_max = k_max;
+  a.ef_default = ef_default;
+  a.ef_cap = ef_cap;
+  a.t = opts.t;
+  a.kappa = opts.kappa;
+  a.tau = opts.tau > 0.f ? opts.tau : 0.92f;
+  a.cutoff = opts.cutoff > 0.f ? opts.cutoff : 1.4f;
+  a.mode = opts.verify_mode;
+  a.width = width;
+  a.hash_bits = hb;
+  a.cmax = cmax;
+  a.vcap = 0;
+  a.out_ids = out_ids;
+  a.out_dist = out_dist;
+  a.stats = opts.stats;
+  a.err = idx->err;
+  a.queue_head = opts.persistent ? idx->queue_head : nullptr;
+  P->shape = sh;
+  P->smem = L.total;
+  P->persistent = opts.persistent != 0;
+  P->grid = (int)nq;
+  if (P->persistent) {
+    const int occ = search_occupancy(idx->tdtype, sh, kBlock, L.total);
+    if (occ < 1) return fail(UHNSW_ECUDA, "uhnsw_search: kernel does not fit (smem %zu)", L.total);
+    P->grid = (int)std::min<int64_t>(nq, (int64_t)occ * idx->num_sms);
+  }
+  return UHNSW_OK;
+}
+
+int enqueue_search(uhnsw_index* idx, const Prepared& P, cudaStream_t st) {
+  if (P.a.nq == 0) return UHNSW_OK;
+  cudaError_t e;
+  if (P.persistent) {
+    e = cudaMemsetAsync(idx->queue_head, 0, 4, st);
+    if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: queue reset");
+  }
+  e = launch_search(idx->tdtype, P.shape, P.a, P.grid, kBlock, P.smem, st);
+  if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: launch");
+  return UHNSW_OK;
+}
+
+}  // namespace
+
+extern "C" int uhnsw_search(uhnsw_index* idx, const float* q, const float* p, const int32_t* k,
+                            const int32_t* ef, int64_t nq, int32_t k_max, int32_t ef_default,
+                            const uhnsw_search_opts* opts, int64_t* out_ids, float* out_dist,
+                            void* stream) {
+  clear_error();
+  Prepared P;
+  int rc = prepare_search(idx, q, p, k, ef, nq, k_max, ef_default, opts, out_ids, out_dist, &P);
+  if (rc != UHNSW_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!opts || !opts->use_graph || nq == 0) return enqueue_search(idx, P, st);
+
+  // CUDA-graph path: capture the launch sequence once per call shape, replay.
+  GraphKey key;
+  std::memset(&key, 0, sizeof(key));
+  key.ptr[0] = q;
+  key.ptr[1] = p;
+  key.ptr[2] = k;
+  key.ptr[3] = ef;
+  key.ptr[4] = out_ids;
+  key.ptr[5] = out_dist;
+  key.ptr[6] = opts->stats;
+  key.nq = nq;
+  key.k_max = k_max;
+  key.ef_default = ef_default;
+  key.opts = *opts;
+  key.stream = stream;
+  std::lock_guard<std::mutex> lock(idx->mu);
+  for (auto& ge : idx->graphs)
+    if (ge.key == key) {
+      cudaError_t e = cudaGraphLaunch(ge.exec, st);
+      return e == cudaSuccess ? UHNSW_OK : cuda_fail(e, "uhnsw_search: cudaGraphLaunch");
+    }
+  cudaStream_t cs = idx->capture_stream;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: begin capture");
+  rc = enqueue_search(idx, P, cs);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cs, &graph);
+  if (rc != UHNSW_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: end capture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: instantiate");
+  if (idx->graphs.size() >= 16) {
+    cudaGraphExecDestroy(idx->graphs.front().exec);
+    idx->graphs.erase(idx->graphs.begin());
+  }
+  idx->graphs.push_back(GraphEntry{key, exec});
+  e = cudaGraphLaunch(exec, st);
+  return e == cudaSuccess ? UHNSW_OK : cuda_fail(e, "uhnsw_search: cudaGraphLaunch");
+}
+
+extern "C" int uhnsw_search_host(uhnsw_index* idx, const float* q, const float* p, const int32_t* k,
+                                 const int32_t* ef, int64_t nq, int32_t k_max, int32_t ef_default,
+                                 const uhnsw_search_opts* opts, int64_t* out_ids, float* out_dist,
+                                 void* stream) {
+  clear_error();
+  if (!idx) return fail(UHNSW_EINVAL, "uhnsw_search_host: index is NULL");
+  if (nq < 0 || nq > INT32_MAX) return fail(UHNSW_EINVAL, "uhnsw_search_host: nq");
+  if (nq == 0) return UHNSW_OK;
+  if (!q || !p || !out_ids || !out_dist) return fail(UHNSW_EINVAL, "uhnsw_search_host: NULL pointer");
+  if (k_max < 1 || k_max > UHNSW_MAX_EF) return fail(UHNSW_EINVAL, "uhnsw_search_host: k_max");
+  const size_t bq = (size_t)nq * idx->d * 4, bp = (size_t)nq * 4, bk = k ? (size_t)nq * 4 : 0,
+               be = ef ? (size_t)nq * 4 : 0, bi = (size_t)nq * k_max * 8,
+               bd = (size_t)nq * k_max * 4;
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t need = al(bq) + al(bp) + al(bk) + al(be) + al(bi) + al(bd);
+  std::lock_guard<std::mutex> lock(idx->mu);
+  if (need > idx->stage_bytes) {
+    cudaFree(idx->stage);
+    idx->stage = nullptr;
+    idx->stage_bytes = 0;
+    cudaError_t e = cudaMalloc(&idx->stage, need);
+    if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search_host: staging");
+    idx->stage_bytes = need;
+  }
+  char* s = (char*)idx->stage;
+  float* dq = (float*)s; s += al(bq);
+  float* dp = (float*)s; s += al(bp);
+  int32_t* dk = k ? (int32_t*)s : nullptr; s += al(bk);
+  int32_t* de = ef ? (int32_t*)s : nullptr; s += al(be);
+  int64_t* di = (int64_t*)s; s += al(bi);
+  float* dd = (float*)s;
+  Prepared P;
+  uhnsw_search_opts o2;
+  std::memset(&o2, 0, sizeof(o2));
+  if (opts) o2 = *opts;
+  o2.use_graph = 0;
+  int rc = prepare_search(idx, dq, dp, dk, de, nq, k_max, ef_default, &o2, di, dd, &P);
+  if (rc != UHNSW_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(dq, q, bq, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dp, p, bp, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && k) e = cudaMemcpyAsync(dk, k, bk, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && ef) e = cudaMemcpyAsync(de, ef, be, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search_host: upload");
+  rc = enqueue_search(idx, P, st);
+  if (rc != UHNSW_OK) return rc;
+  e = cudaMemcpyAsync(out_ids, di, bi, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_dist, dd, bd, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search_host: download");
+  return UHNSW_OK;
+}
+
+extern "C" int uhnsw_verify(uhnsw_index* idx, const float* q, const float* p, const int32_t* cand,
+                            int32_t t, int32_t k, int64_t nq, const uhnsw_search_opts* o,
+                            int64_t* out_ids, float* out_dist, void* stream) {
+  clear_error();
+  if (!idx) return fail(UHNSW_EINVAL, "uhnsw_verify: index is NULL");
+  if (nq < 0 || nq > INT32_MAX) return fail(UHNSW_EINVAL, "uhnsw_verify: nq");
+  if (k < 1 || k > UHNSW_MAX_EF) return fail(UHNSW_EINVAL, "uhnsw_verify: k=%d", k);
+  if (t < 0 || t > 4096) return fail(UHNSW_EINVAL, "uhnsw_verify: t=%d not in [0, 4096]", t);
+  if (nq > 0 && (!q || !p || !out_ids || !out_dist || (t > 0 && !cand)))
+    return fail(UHNSW_EINVAL, "uhnsw_verify: NULL pointer");
+  uhnsw_search_opts opts;
+  std::memset(&opts, 0, sizeof(opts));
+  if (o) opts = *o;
+  if (opts.verify_mode != UHNSW_VERIFY_EXACT && opts.verify_mode != UHNSW_VERIFY_PAPER)
+    return fail(UHNSW_EINVAL, "uhnsw_verify: verify_mode");
+  if (opts.kappa < 0 || !(opts.tau >= 0.f)) return fail(UHNSW_EINVAL, "uhnsw_verify: kappa/tau");
+  if (nq == 0) return UHNSW_OK;
+  QueryArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.base32 = idx->base32;
+  a.n = idx->n;
+  a.d = idx->d;
+  a.d_pad = idx->d_pad;
+  a.q = q;
+  a.p = p;
+  a.nq = nq;
+  a.k_max = k;
+  a.kappa = opts.kappa;
+  a.tau = opts.tau > 0.f ? opts.tau : 0.92f;
+  a.mode = opts.verify_mode;
+  a.cmax = kBlock / 8;
+  a.vcap = std::max(t, 1);
+  a.out_ids = out_ids;
+  a.out_dist = out_dist;
+  a.stats = opts.stats;
+  a.err = idx->err;
+  a.cand = cand;
+  a.cand_t = t;
+  const SmemLayout L(idx->d_pad, 0, 0, a.cmax, k, a.vcap);
+  cudaError_t e = launch_verify(a, kBlock, L.total, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "uhnsw_verify: launch");
+  return UHNSW_OK;
+}
+
+extern "C" int uhnsw_exact(uhnsw_index* idx, const float* q, const float* p, int64_t nq, int32_t k,
+                           int64_t* out_ids, float* out_dist, void* stream) {
+  clear_error();
+  if (!idx) return fail(UHNSW_EINVAL, "uhnsw_exact: index is NULL");
+  if (nq < 0 || nq > INT32_MAX / 2) return fail(UHNSW_EINVAL, "uhnsw_exact: nq");
+  if (k < 1 || k > 256) return fail(UHNSW_EINVAL, "uhnsw_exact: k=%d not in [1, 256]", k);
+  if (nq > 0 && (!q || !p || !out_ids || !out_dist)) return fail(UHNSW_EINVAL, "uhnsw_exact: NULL pointer");
+  if (nq == 0) return UHNSW_OK;
+  const int ns = exact_workspace_slices(idx->n, nq, k, idx->num_sms);
+  const size_t need = (size_t)ns * nq * k * 8;
+  std::lock_guard<std::mutex> lock(idx->mu);
+  if (need > idx->exact_ws_bytes) {
+    cudaFree(idx->exact_ws);
+    idx->exact_ws = nullptr;
+    idx->exact_ws_bytes = 0;
+    cudaError_t e = cudaMalloc(&idx->exact_ws, need);
+    if (e != cudaSuccess) return cuda_fail(e, "uhnsw_exact: workspace");
+    idx->exact_ws_bytes = need;
+  }
+  float* pd = (float*)idx->exact_ws;
+  int32_t* pi = (int32_t*)((char*)idx->exact_ws + (size_t)ns * nq * k * 4);
+  cudaError_t e = launch_exact(idx->base32, idx->n, idx->d, idx->d_pad, q, p, nq, k, ns, pd, pi,
+                               out_ids, out_dist, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "uhnsw_exact: launch");
+  return UHNSW_OK;
+}
+
+extern "C" int uhnsw_index_info(const uhnsw_index* idx, int64_t* n, int32_t* d, int32_t* d_pad,
+                                int64_t* device_bytes, int32_t* max_degree0) {
+  clear_error();
+  if (!idx) return fail(UHNSW_EINVAL, "uhnsw_index_info: index is NULL");
+  if (n) *n = idx->n;
+  if (d) *d = idx->d;
+  if (d_pad) *d_pad = idx->d_pad;
+  if (device_bytes) *device_bytes = idx->bytes;
+  if (max_degree0) *max_degree0 = std::max(idx->g[0].deg0, idx->g[1].deg0);
+  return UHNSW_OK;
+}
+
+extern "C" int uhnsw_device_status(uhnsw_index* idx) {
+  clear_error();
+  if (!idx) return fail(UHNSW_EINVAL, "uhnsw_device_status: index is NULL");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "uhnsw_device_status: synchronize");
+  int32_t v = 0;
+  e = cudaMemcpy(&v, idx->err, 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(idx->err, 0, 4);
+  if (e != cudaSuccess) return cuda_fail(e, "uhnsw_device_status: read");
+  if (v != 0) return fail(v, "uhnsw_device_status: device recorded error %d", v);
+  return UHNSW_OK;
+}
+
+extern "C" void uhnsw_free(uhnsw_index* idx) { delete idx; }

@@ -1,0 +1,51 @@
+// Host-side launch interfaces of the device code (one translation unit per
+// storage type keeps the build parallel).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "query_kernels.cuh"
+
+namespace uhnsw_dev {
+
+// Team shape of the traversal distance: TEAM lanes per row, CPL 16-byte chunks
+// per lane; the first shape whose TEAM * CPL covers the row is used.
+struct TeamShape {
+  int team, cpl;
+};
+
+// Returns false if no compiled shape covers rows of `chunks` 16-byte chunks.
+bool pick_shape(uhnsw_dtype dt, int chunks, TeamShape* out);
+
+// Launch the fused search kernel: one block per query (grid = nq) or, with
+// a.queue_head set, `grid` persistent blocks.
+cudaError_t launch_search(uhnsw_dtype dt, TeamShape sh, const QueryArgs& a, int grid, int block,
+                          size_t smem, cudaStream_t st);
+
+// Resident blocks per SM of the search kernel for this shape and smem size.
+int search_occupancy(uhnsw_dtype dt, TeamShape sh, int block, size_t smem);
+
+cudaError_t launch_verify(const QueryArgs& a, int block, size_t smem, cudaStream_t st);
+
+cudaError_t launch_convert(const float* src, void* dst, uhnsw_dtype dt, int64_t count,
+                           cudaStream_t st);
+
+int exact_workspace_slices(int64_t n, int64_t nq, int k, int num_sms);
+cudaError_t launch_exact(const float* base, int64_t n, int d, int d_pad, const float* q,
+                         const float* p, int64_t nq, int k, int nslices, float* part_d,
+                         int32_t* part_i, int64_t* out_ids, float* out_dist, cudaStream_t st);
+
+// per-storage-type entry points (defined in search_<type>.cu)
+cudaError_t launch_search_f32(TeamShape sh, const QueryArgs& a, int grid, int block, size_t smem,
+                              cudaStream_t st);
+cudaError_t launch_search_f16(TeamShape sh, const QueryArgs& a, int grid, int block, size_t smem,
+                              cudaStream_t st);
+cudaError_t launch_search_bf16(TeamShape sh, const QueryArgs& a, int grid, int block, size_t smem,
+                               cudaStream_t st);
+int occupancy_f32(TeamShape sh, int block, size_t smem);
+int occupancy_f16(TeamShape sh, int block, size_t smem);
+int occupancy_bf16(TeamShape sh, int block, size_t smem);
+
+}  // namespace uhnsw_dev

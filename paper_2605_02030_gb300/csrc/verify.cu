@@ -1,0 +1,68 @@
+// Verification-only kernel launch and the storage conversion kernel.
+#include <cuda_runtime.h>
+
+#include "launch.h"
+
+namespace uhnsw_dev {
+
+cudaError_t launch_verify(const QueryArgs& a, int block, size_t smem, cudaStream_t st) {
+  if (block != 128) return cudaErrorInvalidValue;
+  auto kern = uhnsw_verify_kernel<128>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)a.nq, 128, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// FP32 master rows -> FP16 / BF16 traversal rows (round to nearest even).
+__global__ void convert_kernel(const float* __restrict__ src, void* dst, int dt, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float x = src[i];
+    if (dt == UHNSW_F16) reinterpret_cast<__half*>(dst)[i] = __float2half_rn(x);
+    else reinterpret_cast<__nv_bfloat16*>(dst)[i] = __float2bfloat16_rn(x);
+  }
+}
+
+cudaError_t launch_convert(const float* src, void* dst, uhnsw_dtype dt, int64_t count,
+                           cudaStream_t st) {
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks < 1) blocks = 1;
+  convert_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dst, (int)dt, count);
+  return cudaGetLastError();
+}
+
+bool pick_shape(uhnsw_dtype dt, int chunks, TeamShape* out) {
+  static const TeamShape f32[] = {{8, 1}, {16, 2}, {32, 2}, {32, 4}, {32, 8}, {32, 16}};
+  static const TeamShape f16[] = {{8, 1}, {16, 1}, {32, 1}, {32, 2}, {32, 4}, {32, 8}};
+  const TeamShape* list = dt == UHNSW_F32 ? f32 : f16;
+  const int cnt = 6;
+  for (int i = 0; i < cnt; ++i)
+    if (list[i].team * list[i].cpl >= chunks) {
+      *out = list[i];
+      return true;
+    }
+  return false;
+}
+
+cudaError_t launch_search(uhnsw_dtype dt, TeamShape sh, const QueryArgs& a, int grid, int block,
+                          size_t smem, cudaStream_t st) {
+  switch (dt) {
+    case UHNSW_F32: return launch_search_f32(sh, a, grid, block, smem, st);
+    case UHNSW_F16: return launch_search_f16(sh, a, grid, block, smem, st);
+    case UHNSW_BF16: return launch_search_bf16(sh, a, grid, block, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int search_occupancy(uhnsw_dtype dt, TeamShape sh, int block, size_t smem) {
+  switch (dt) {
+    case UHNSW_F32: return occupancy_f32(sh, block, smem);
+    case UHNSW_F16: return occupancy_f16(sh, block, smem);
+    case UHNSW_BF16: return occupancy_bf16(sh, block, smem);
+  }
+  return 0;
+}
+
+}  // namespace uhnsw_dev

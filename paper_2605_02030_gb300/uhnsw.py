@@ -1,0 +1,328 @@
+"""Python binding of the C ABI in include/uhnsw.h (argument marshalling only).
+
+Every step of the query path runs in libuhnsw.so's CUDA kernels; this module
+passes pointers and sizes.  torch provides device memory and streams.  The
+library must have been built (``paper_2605_02030_gb300.build()``); a missing
+library raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+MAX_LEVELS = 16
+MAX_EF = 512
+NSTATS = 8
+STAT_NAMES = ("nb", "np", "terms", "expansions", "resets", "status", "graph", "adj")
+DTYPES = {"f32": 0, "f16": 1, "bf16": 2}
+MODES = {"exact": 0, "paper": 1}
+
+_lib = None
+
+
+class UHNSWError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"uhnsw error {code}: {msg}")
+        self.code = code
+
+
+class _Graph(C.Structure):
+    _fields_ = [
+        ("num_levels", C.c_int32),
+        ("entry_point", C.c_int32),
+        ("max_degree0", C.c_int32),
+        ("max_degree", C.c_int32),
+        ("level_count", C.c_void_p),
+        ("level_nodes", C.c_void_p * MAX_LEVELS),
+        ("level_offsets", C.c_void_p * MAX_LEVELS),
+        ("level_nbrs", C.c_void_p * MAX_LEVELS),
+    ]
+
+
+class _LoadOpts(C.Structure):
+    _fields_ = [("traverse_dtype", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class _SearchOpts(C.Structure):
+    _fields_ = [
+        ("t", C.c_int32),
+        ("kappa", C.c_int32),
+        ("tau", C.c_float),
+        ("cutoff", C.c_float),
+        ("verify_mode", C.c_int32),
+        ("search_width", C.c_int32),
+        ("persistent", C.c_int32),
+        ("use_graph", C.c_int32),
+        ("ef_max", C.c_int32),
+        ("block_threads", C.c_int32),
+        ("stats", C.c_void_p),
+        ("reserved", C.c_int32 * 4),
+    ]
+
+
+EXPORTS = ("uhnsw_load", "uhnsw_search", "uhnsw_search_host", "uhnsw_verify", "uhnsw_exact",
+           "uhnsw_index_info", "uhnsw_device_status", "uhnsw_free", "uhnsw_last_error",
+           "uhnsw_build_graph", "uhnsw_built_graph", "uhnsw_built_free")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library():
+    """Loads libuhnsw.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built: run paper_2605_02030_gb300.build() first")
+    lib = C.CDLL(path)
+    P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
+    lib.uhnsw_last_error.restype = C.c_char_p
+    lib.uhnsw_last_error.argtypes = []
+    lib.uhnsw_load.restype = C.c_int
+    lib.uhnsw_load.argtypes = [P, I64, I32, P, P, P, P]
+    lib.uhnsw_search.restype = C.c_int
+    lib.uhnsw_search.argtypes = [P, P, P, P, P, I64, I32, I32, P, P, P, P]
+    lib.uhnsw_search_host.restype = C.c_int
+    lib.uhnsw_search_host.argtypes = [P, P, P, P, P, I64, I32, I32, P, P, P, P]
+    lib.uhnsw_verify.restype = C.c_int
+    lib.uhnsw_verify.argtypes = [P, P, P, P, I32, I32, I64, P, P, P, P]
+    lib.uhnsw_exact.restype = C.c_int
+    lib.uhnsw_exact.argtypes = [P, P, P, I64, I32, P, P, P]
+    lib.uhnsw_index_info.restype = C.c_int
+    lib.uhnsw_index_info.argtypes = [P, P, P, P, P, P]
+    lib.uhnsw_device_status.restype = C.c_int
+    lib.uhnsw_device_status.argtypes = [P]
+    lib.uhnsw_free.restype = None
+    lib.uhnsw_free.argtypes = [P]
+    lib.uhnsw_build_graph.restype = C.c_int
+    lib.uhnsw_build_graph.argtypes = [P, I64, I32, I32, I32, I32, P, I32, P]
+    lib.uhnsw_built_graph.restype = C.c_int
+    lib.uhnsw_built_graph.argtypes = [P, P]
+    lib.uhnsw_built_free.restype = None
+    lib.uhnsw_built_free.argtypes = [P]
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise UHNSWError(rc, load_library().uhnsw_last_error().decode(errors="replace"))
+
+
+def _np_ptr(a) -> C.c_void_p:
+    return C.c_void_p(a.ctypes.data) if a is not None else C.c_void_p(0)
+
+
+def _t_ptr(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _stream_ptr(stream) -> C.c_void_p:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+# ----------------------------------------------------------------- graph building
+def build_graph(base: np.ndarray, metric: int, M: int, ef_construction: int, levels: np.ndarray,
+                threads: int = 0) -> dict:
+    """HNSW graph under L1 (metric=1) or squared L2 (metric=2), built on the host
+    by the library's multi-threaded insertion; returned as a CSR dict
+    {num_levels, entry_point, max_degree0, max_degree, n, levels: [{nodes,
+    offsets, nbrs}]} with level 0 listing every node."""
+    lib = load_library()
+    base = np.ascontiguousarray(base, np.float32)
+    levels = np.ascontiguousarray(levels, np.int32)
+    n, d = base.shape
+    h = C.c_void_p(0)
+    _check(lib.uhnsw_build_graph(_np_ptr(base), n, d, metric, M, ef_construction, _np_ptr(levels),
+                                 threads, C.byref(h)))
+    try:
+        g = _Graph()
+        _check(lib.uhnsw_built_graph(h, C.byref(g)))
+        L = g.num_levels
+        counts = np.ctypeslib.as_array(C.cast(g.level_count, C.POINTER(C.c_int32)), shape=(L,)).copy()
+        out = {"num_levels": L, "entry_point": g.entry_point, "max_degree0": g.max_degree0,
+               "max_degree": g.max_degree, "n": n, "levels": []}
+        for l in range(L):
+            cnt = int(counts[l])
+            offs = np.ctypeslib.as_array(C.cast(g.level_offsets[l], C.POINTER(C.c_int64)),
+                                         shape=(cnt + 1,)).copy()
+            ne = int(offs[-1])
+            nbrs = (np.ctypeslib.as_array(C.cast(g.level_nbrs[l], C.POINTER(C.c_int32)),
+                                          shape=(ne,)).copy() if ne else np.zeros(0, np.int32))
+            if l == 0:
+                nodes = np.arange(n, dtype=np.int32)
+            else:
+                nodes = np.ctypeslib.as_array(C.cast(g.level_nodes[l], C.POINTER(C.c_int32)),
+                                              shape=(cnt,)).copy()
+            out["levels"].append({"nodes": nodes, "offsets": offs, "nbrs": nbrs})
+        return out
+    finally:
+        lib.uhnsw_built_free(h)
+
+
+def _graph_struct(g: dict | None):
+    if g is None:
+        return None, []
+    keep = []
+    s = _Graph()
+    s.num_levels = g["num_levels"]
+    s.entry_point = g["entry_point"]
+    s.max_degree0 = g["max_degree0"]
+    s.max_degree = g["max_degree"]
+    cnt = np.array([len(lv["offsets"]) - 1 for lv in g["levels"]], np.int32)
+    keep.append(cnt)
+    s.level_count = cnt.ctypes.data
+    for l, lv in enumerate(g["levels"]):
+        nodes = np.ascontiguousarray(lv["nodes"], np.int32)
+        offs = np.ascontiguousarray(lv["offsets"], np.int64)
+        nbrs = np.ascontiguousarray(lv["nbrs"], np.int32)
+        if nbrs.size == 0:
+            nbrs = np.zeros(1, np.int32)
+        keep += [nodes, offs, nbrs]
+        s.level_nodes[l] = nodes.ctypes.data
+        s.level_offsets[l] = offs.ctypes.data
+        s.level_nbrs[l] = nbrs.ctypes.data
+    return s, keep
+
+
+# ----------------------------------------------------------------- index
+class Index:
+    """A loaded U-HNSW index (base vectors + G1 + G2) on the current CUDA device."""
+
+    def __init__(self, base: np.ndarray, g1: dict | None, g2: dict | None,
+                 traverse_dtype: str = "f32"):
+        lib = load_library()
+        base = np.ascontiguousarray(base, np.float32)
+        self.n, self.d = base.shape
+        self.traverse_dtype = traverse_dtype
+        s1, k1 = _graph_struct(g1)
+        s2, k2 = _graph_struct(g2)
+        opts = _LoadOpts()
+        opts.traverse_dtype = DTYPES[traverse_dtype]
+        h = C.c_void_p(0)
+        _check(lib.uhnsw_load(_np_ptr(base), self.n, self.d,
+                              C.byref(s1) if s1 is not None else None,
+                              C.byref(s2) if s2 is not None else None, C.byref(opts), C.byref(h)))
+        self._h = h
+        del k1, k2
+
+    # -- helpers
+    def _opts(self, t=0, kappa=0, tau=0.0, cutoff=0.0, mode="exact", width=1, persistent=False,
+              use_graph=False, ef_max=0, stats_t=None, block_threads=0):
+        o = _SearchOpts()
+        o.t, o.kappa, o.tau, o.cutoff = int(t), int(kappa), float(tau), float(cutoff)
+        o.verify_mode = MODES[mode] if isinstance(mode, str) else int(mode)
+        o.search_width = int(width)
+        o.persistent = int(bool(persistent))
+        o.use_graph = int(bool(use_graph))
+        o.ef_max = int(ef_max)
+        o.block_threads = int(block_threads)
+        o.stats = stats_t.data_ptr() if stats_t is not None else None
+        return o
+
+    def search(self, q, p, k=10, ef=64, *, k_max: int | None = None, t: int = 0, tau: float = 0.0,
+               kappa: int = 0, cutoff: float = 0.0, mode: str = "exact", width: int = 1,
+               persistent: bool = False, use_graph: bool = False, ef_max: int = 0,
+               stats: bool = False, out=None, stream=None):
+        """Algorithm 1 on device tensors.  q: float32 [nq, d] cuda; p: float32 [nq];
+        k / ef: int (same for all) or int32 [nq] tensors.  Returns (ids int64
+        [nq, k_max], dist float32 [nq, k_max], stats int32 [nq, 8] or None)."""
+        import torch
+        lib = load_library()
+        nq = q.shape[0]
+        k_t = k if torch.is_tensor(k) else None
+        ef_t = ef if torch.is_tensor(ef) else None
+        if k_max is None:
+            k_max = int(k_t.max().item()) if k_t is not None and nq else int(k if k_t is None else 1)
+        ef_default = int(ef) if ef_t is None else max(1, int(ef_max) or MAX_EF)
+        if out is None:
+            ids = torch.empty((nq, k_max), dtype=torch.int64, device=q.device)
+            dist = torch.empty((nq, k_max), dtype=torch.float32, device=q.device)
+        else:
+            ids, dist = out
+        st = torch.zeros((nq, NSTATS), dtype=torch.int32, device=q.device) if stats else None
+        o = self._opts(t, kappa, tau, cutoff, mode, width, persistent, use_graph, ef_max, st)
+        _check(lib.uhnsw_search(self._h, _t_ptr(q), _t_ptr(p), _t_ptr(k_t), _t_ptr(ef_t), nq,
+                                k_max, ef_default, C.byref(o), _t_ptr(ids), _t_ptr(dist),
+                                _stream_ptr(stream)))
+        return ids, dist, st
+
+    def search_host(self, q: np.ndarray, p: np.ndarray, k=10, ef=64, *, k_max: int | None = None,
+                    out=None, stream=None, **kw):
+        """uhnsw_search_host: host (pinned or pageable) arrays in and out."""
+        lib = load_library()
+        q = np.ascontiguousarray(q, np.float32)
+        p = np.ascontiguousarray(p, np.float32)
+        nq = q.shape[0]
+        k_a = np.ascontiguousarray(k, np.int32) if isinstance(k, np.ndarray) else None
+        ef_a = np.ascontiguousarray(ef, np.int32) if isinstance(ef, np.ndarray) else None
+        if k_max is None:
+            k_max = int(k_a.max()) if k_a is not None else int(k)
+        ef_default = int(ef) if ef_a is None else max(1, int(kw.get("ef_max", 0)) or MAX_EF)
+        if out is None:
+            ids = np.empty((nq, k_max), np.int64)
+            dist = np.empty((nq, k_max), np.float32)
+        else:
+            ids, dist = out
+        o = self._opts(**{x: kw[x] for x in ("t", "kappa", "tau", "cutoff", "mode", "width",
+                                             "persistent", "ef_max") if x in kw})
+        _check(lib.uhnsw_search_host(self._h, _np_ptr(q), _np_ptr(p), _np_ptr(k_a), _np_ptr(ef_a),
+                                     nq, k_max, ef_default, C.byref(o), _np_ptr(ids),
+                                     _np_ptr(dist), _stream_ptr(stream)))
+        return ids, dist
+
+    def verify(self, q, p, cand, k: int, *, mode: str = "exact", kappa: int = 0, tau: float = 0.0,
+               stats: bool = False, stream=None):
+        """Verification only on candidate lists cand int32 [nq, t] (-1 = absent)."""
+        import torch
+        lib = load_library()
+        nq, t = cand.shape
+        ids = torch.empty((nq, k), dtype=torch.int64, device=q.device)
+        dist = torch.empty((nq, k), dtype=torch.float32, device=q.device)
+        st = torch.zeros((nq, NSTATS), dtype=torch.int32, device=q.device) if stats else None
+        o = self._opts(kappa=kappa, tau=tau, mode=mode, stats_t=st)
+        _check(lib.uhnsw_verify(self._h, _t_ptr(q), _t_ptr(p), _t_ptr(cand), t, k, nq, C.byref(o),
+                                _t_ptr(ids), _t_ptr(dist), _stream_ptr(stream)))
+        return ids, dist, st
+
+    def exact(self, q, p, k: int, stream=None):
+        """Exhaustive L_p k-NN on the GPU: (ids int64 [nq, k], dist float32 [nq, k])."""
+        import torch
+        lib = load_library()
+        nq = q.shape[0]
+        ids = torch.empty((nq, k), dtype=torch.int64, device=q.device)
+        dist = torch.empty((nq, k), dtype=torch.float32, device=q.device)
+        _check(lib.uhnsw_exact(self._h, _t_ptr(q), _t_ptr(p), nq, k, _t_ptr(ids), _t_ptr(dist),
+                               _stream_ptr(stream)))
+        return ids, dist
+
+    def info(self) -> dict:
+        lib = load_library()
+        n, d, dp, b, m0 = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int64(), C.c_int32()
+        _check(lib.uhnsw_index_info(self._h, C.byref(n), C.byref(d), C.byref(dp), C.byref(b),
+                                    C.byref(m0)))
+        return {"n": n.value, "d": d.value, "d_pad": dp.value, "device_bytes": b.value,
+                "max_degree0": m0.value}
+
+    def device_status(self) -> int:
+        return load_library().uhnsw_device_status(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().uhnsw_free(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,283 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Verification: ids identical to the oracle's exhaustive top-K over the same
+candidate set except near-ties within 1e-5 relative; distances within 2e-5
+relative.  Deterministic search (one expansion per step): the beam equals the
+oracle's HNSW search on the same CSR id for id (integer / grid data make the
+FP32 base distances exact).  Sizes span several tiles and ragged tails."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_02030_gb300 import inputs as I
+
+from helpers import check_topk, oracle_graphs, workload_arrays
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def U():
+    import paper_2605_02030_gb300 as pkg
+    pkg.build()
+    from paper_2605_02030_gb300 import uhnsw
+    uhnsw.load_library()
+    return uhnsw
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+# ------------------------------------------------------------------ verification
+@pytest.fixture(scope="module")
+def mix_small():
+    return workload_arrays("mixture10k", 2000, 24)
+
+
+@pytest.fixture(scope="module")
+def sift_small():
+    return workload_arrays("sift1m", 3000, 24)
+
+
+@pytest.mark.parametrize("which", ["mix", "sift"])
+@pytest.mark.parametrize("k,t", [(1, 17), (10, 64), (10, 301), (100, 300)])
+def test_verify_exact_matches_oracle(U, mix_small, sift_small, which, k, t):
+    w, base, qs, p, _, _ = mix_small if which == "mix" else sift_small
+    nq = len(qs)
+    pv = p.copy()
+    pv[:6] = [0.5, 1.5, 1.0, 2.0, 0.51, 1.93]      # the SFU-free / one-sqrt cases
+    cand = I.random_candidates(len(base), nq, t, seed=11 + t, missing_frac=0.2)
+    idx = U.Index(base, None, oracle_graphs("mixture10k", 2000, 24)[1] if which == "mix" else
+                  oracle_graphs("sift1m", 3000, 24, M=8, ef_construction=40)[1])
+    ids, dist, st = idx.verify(dev(qs), dev(pv), dev(cand), k, stats=True)
+    ids, dist, st = ids.cpu().numpy(), dist.cpu().numpy(), st.cpu().numpy()
+    for i in range(nq):
+        rid, rS, _ = oracle.verify_exact(base, qs[i], pv[i], cand[i], k)
+        check_topk(base, qs[i], pv[i], ids[i], dist[i], rid, k, f"q{i}")
+        assert st[i, 5] == 0
+        assert st[i, 1] == (cand[i] >= 0).sum()       # every valid candidate started
+    # the partial-sum drop skips terms once the k-th best is known
+    if t >= 64:
+        assert st[:, 2].sum() < ((cand >= 0).sum(axis=1) * w.d).sum()
+    idx.close()
+
+
+@pytest.mark.parametrize("tau", [0.0, 0.5, 0.92, 1.0, 1.5])
+@pytest.mark.parametrize("kappa", [0, 3, 25])
+def test_verify_paper_mode_matches_oracle(U, sift_small, tau, kappa):
+    w, base, qs, p, _, _ = sift_small
+    k, t = 10, 120
+    nq = len(qs)
+    cand = I.random_candidates(len(base), nq, t, seed=5)
+    # candidate order matters in Algorithm 1: sort by L1 like a real C
+    for i in range(nq):
+        dl1 = np.abs(base[cand[i]] - qs[i]).sum(1)
+        cand[i] = cand[i][np.lexsort((cand[i], dl1))]
+    idx = U.Index(base, None, oracle_graphs("sift1m", 3000, 24, M=8, ef_construction=40)[1])
+    ids, dist, st = idx.verify(dev(qs), dev(p), dev(cand), k, mode="paper", kappa=kappa, tau=tau,
+                               stats=True)
+    ids, dist, st = ids.cpu().numpy(), dist.cpu().numpy(), st.cpu().numpy()
+    same_np = 0
+    for i in range(nq):
+        rid, rS, nlp, nb = oracle.verify_paper(base, qs[i], p[i], cand[i], k, kappa or k, tau)
+        ties = check_topk(base, qs[i], p[i], ids[i], dist[i], rid, k, f"q{i}")
+        same_np += int(st[i, 1] == nlp)
+        if ties == 0:
+            assert st[i, 1] == nlp, f"q{i}: {st[i, 1]} L_p candidates vs oracle {nlp}"
+    assert same_np >= nq - 1
+    idx.close()
+
+
+def test_verify_degenerate(U, sift_small):
+    w, base, qs, p, _, _ = sift_small
+    idx = U.Index(base, None, oracle_graphs("sift1m", 3000, 24, M=8, ef_construction=40)[1])
+    cand = np.full((3, 5), -1, np.int32)
+    cand[1, 2] = 7
+    pv = np.array([0.7, 1.2, 2.0], np.float32)
+    ids, dist, _ = idx.verify(dev(qs[:3]), dev(pv), dev(cand), 4)
+    ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
+    assert (ids[0] == -1).all() and np.isinf(dist[0]).all()
+    assert ids[1].tolist() == [7, -1, -1, -1]
+    assert dist[1, 0] == pytest.approx(oracle.lp_sum(base[7], qs[1], 1.2) ** (1 / np.float32(1.2)),
+                                       rel=2e-5)
+    # invalid p -> that query alone is padded and flagged
+    pv = np.array([0.0, 2.5, 1.0], np.float32)
+    cand = np.tile(np.arange(5, dtype=np.int32), (3, 1))
+    ids, dist, st = idx.verify(dev(qs[:3]), dev(pv), dev(cand), 2, stats=True)
+    st = st.cpu().numpy()
+    assert st[0, 5] == -1 and st[1, 5] == -1 and st[2, 5] == 0
+    assert (ids.cpu().numpy()[:2] == -1).all()
+    # nq = 0 is a no-op
+    e = torch.empty((0, 128), device="cuda")
+    idx.verify(e, torch.empty(0, device="cuda"), torch.empty((0, 5), dtype=torch.int32, device="cuda"), 2)
+    idx.close()
+
+
+# ------------------------------------------------------------------ exact k-NN
+@pytest.mark.parametrize("which,k", [("mix", 1), ("mix", 10), ("sift", 10), ("sift", 100)])
+def test_exact_knn_matches_oracle(U, mix_small, sift_small, which, k):
+    w, base, qs, p, _, _ = mix_small if which == "mix" else sift_small
+    pv = p.copy()
+    pv[:2] = [1.0, 2.0]
+    idx = U.Index(base, *(oracle_graphs("mixture10k", 2000, 24) if which == "mix" else
+                          oracle_graphs("sift1m", 3000, 24, M=8, ef_construction=40)))
+    ids, dist = idx.exact(dev(qs), dev(pv), k)
+    ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
+    rid, rS = oracle.exact_knn(base, qs, pv, k)
+    for i in range(len(qs)):
+        check_topk(base, qs[i], pv[i], ids[i], dist[i], rid[i], k, f"q{i}")
+    idx.close()
+
+
+# ------------------------------------------------------------------ search
+CASES = {
+    # name: (workload, n, nq, grid, kw)
+    "mixture_grid": ("mixture10k", 4000, 40, 1 / 16, {}),
+    "sift": ("sift1m", 6000, 40, 0.0, dict(M=12, ef_construction=80)),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def search_case(request, U):
+    name, n, nq, grid, kw = CASES[request.param]
+    w, base, qs, p, k, ef = workload_arrays(name, n, nq, grid, **kw)
+    g1, g2 = oracle_graphs(name, n, nq, grid, **kw)
+    return request.param, w, base, qs, p, g1, g2
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("ef", [16, 50, 128])
+def test_deterministic_beam_equals_oracle_search(U, search_case, dtype, ef):
+    """p = 1 and p = 2 return the first k beam entries directly: with k = ef
+    this is the whole beam, which must equal the oracle's SEARCH-LAYER result
+    on the same graph id for id (base distances exact on this data)."""
+    cname, w, base, qs, p, g1, g2 = search_case
+    if dtype == "bf16" and cname == "mixture_grid":
+        pytest.skip("grid values are not exact in BF16")
+    idx = U.Index(base, g1, g2, traverse_dtype=dtype)
+    nq = len(qs)
+    for pp, metric, g in ((1.0, 1, g1), (2.0, 2, g2)):
+        pv = np.full(nq, pp, np.float32)
+        ids, dist, st = idx.search(dev(qs), dev(pv), k=ef, ef=ef, stats=True)
+        ids, dist, st = ids.cpu().numpy(), dist.cpu().numpy(), st.cpu().numpy()
+        for i in range(nq):
+            rid, rd, _ = oracle.hnsw_search(g, base, qs[i], metric, ef, ef)
+            np.testing.assert_array_equal(ids[i], rid, err_msg=f"{cname} {dtype} p={pp} q{i}")
+            want = rd if metric == 1 else np.sqrt(rd)
+            np.testing.assert_allclose(dist[i][rid >= 0], want[rid >= 0], rtol=1e-6)
+        assert (st[:, 6] == metric).all() and (st[:, 5] == 0).all()
+    idx.close()
+
+
+@pytest.mark.parametrize("mode", ["exact", "paper"])
+def test_uhnsw_query_matches_oracle(U, search_case, mode):
+    """Algorithm 1 end to end (routing, KnnSearch, verification) against the
+    oracle on the same graphs, per-query p (including p = 1, 2 and the
+    1.4 cutoff on both sides), k = 10, ef = 48, t = ef."""
+    cname, w, base, qs, p, g1, g2 = search_case
+    nq = len(qs)
+    pv = p.copy()
+    pv[:5] = [1.0, 2.0, 1.4, np.nextafter(np.float32(1.4), np.float32(2)), 0.5]
+    idx = U.Index(base, g1, g2)
+    ids, dist, st = idx.search(dev(qs), dev(pv), k=10, ef=48, mode=mode, stats=True)
+    ids, dist, st = ids.cpu().numpy(), dist.cpu().numpy(), st.cpu().numpy()
+    for i in range(nq):
+        rid, rd, rst = oracle.uhnsw_query(g1, g2, base, qs[i], pv[i], 10, 48,
+                                          mode=0 if mode == "exact" else 1)
+        check_topk(base, qs[i], pv[i], ids[i], dist[i], rid, 10, f"{cname} q{i} p={pv[i]}")
+        exp_graph = 1 if pv[i] == 1.0 else 2 if pv[i] == 2.0 else (1 if pv[i] <= np.float32(1.4) else 2)
+        assert st[i, 6] == exp_graph
+    idx.close()
+
+
+def test_search_per_query_k_ef_and_padding(U, search_case):
+    cname, w, base, qs, p, g1, g2 = search_case
+    nq = len(qs)
+    rng = np.random.default_rng(3)
+    k = rng.integers(1, 21, nq).astype(np.int32)
+    ef = np.maximum(rng.integers(8, 90, nq), 1).astype(np.int32)
+    idx = U.Index(base, g1, g2)
+    ids, dist, _ = idx.search(dev(qs), dev(p), k=dev(k), ef=dev(ef), k_max=24, ef_max=128)
+    ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
+    for i in range(nq):
+        rid, rd, _ = oracle.uhnsw_query(g1, g2, base, qs[i], p[i], int(k[i]), int(ef[i]))
+        check_topk(base, qs[i], p[i], ids[i], dist[i], rid, int(k[i]), f"q{i}")
+        assert (ids[i, k[i]:] == -1).all() and np.isinf(dist[i, k[i]:]).all()
+    idx.close()
+
+
+def test_search_forms_agree_bitwise(U, search_case):
+    """Plain launch, persistent launch, CUDA-graph replay, host-buffer call and
+    each query alone vs in the batch: identical results (deterministic mode)."""
+    cname, w, base, qs, p, g1, g2 = search_case
+    idx = U.Index(base, g1, g2, traverse_dtype="f16")
+    q, pp = dev(qs), dev(p)
+    a_ids, a_d, _ = idx.search(q, pp, k=10, ef=40)
+    b_ids, b_d, _ = idx.search(q, pp, k=10, ef=40, persistent=True)
+    c_ids, c_d, _ = idx.search(q, pp, k=10, ef=40, persistent=True, use_graph=True)
+    c2_ids, c2_d, _ = idx.search(q, pp, k=10, ef=40, persistent=True, use_graph=True,
+                                 out=(c_ids, c_d))
+    h_ids, h_d = idx.search_host(qs, p, k=10, ef=40)
+    torch.cuda.synchronize()
+    for x, y in ((b_ids, b_d), (c_ids, c_d), (c2_ids, c2_d)):
+        assert torch.equal(a_ids, x) and torch.equal(a_d, y)
+    np.testing.assert_array_equal(a_ids.cpu().numpy(), h_ids)
+    np.testing.assert_array_equal(a_d.cpu().numpy(), h_d)
+    for i in (0, 7, len(qs) - 1):
+        s_ids, s_d, _ = idx.search(q[i:i + 1], pp[i:i + 1], k=10, ef=40)
+        assert torch.equal(s_ids[0], a_ids[i]) and torch.equal(s_d[0], a_d[i])
+    idx.close()
+
+
+def test_wide_search_recall_and_validity(U, search_case):
+    """Several expansions per step (not HNSW's sequential order): results stay
+    valid and recall against the exact answer stays high."""
+    cname, w, base, qs, p, g1, g2 = search_case
+    idx = U.Index(base, g1, g2)
+    gt, _ = oracle.exact_knn(base, qs, p, 10)
+    for width in (2, 4):
+        ids, dist, _ = idx.search(dev(qs), dev(p), k=10, ef=64, width=width)
+        ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
+        for i in range(len(qs)):
+            got = ids[i][ids[i] >= 0]
+            assert len(set(got.tolist())) == len(got)
+            for j, v in enumerate(got):
+                exp = oracle.lp_sum(base[v], qs[i], float(p[i])) ** (1 / float(p[i]))
+                assert abs(dist[i, j] - exp) <= 2e-5 * exp
+        assert oracle.recall(ids, gt) >= 0.9
+    idx.close()
+
+
+def test_search_invalid_queries_and_edges(U, search_case):
+    cname, w, base, qs, p, g1, g2 = search_case
+    idx = U.Index(base, g1, None)
+    pv = np.array([0.8, -1.0, 1.9, np.nan], np.float32)   # 1.9 routes to the missing G2
+    ids, dist, st = idx.search(dev(qs[:4]), dev(pv), k=5, ef=20, stats=True)
+    st = st.cpu().numpy()
+    assert st[0, 5] == 0 and (st[1:, 5] == -1).all()
+    assert (ids.cpu().numpy()[1:] == -1).all()
+    # k above ef: the beam grows to k
+    ids, dist, _ = idx.search(dev(qs[:2]), dev(np.array([0.9, 0.9], np.float32)), k=30, ef=8)
+    assert (ids.cpu().numpy() >= 0).all()
+    # empty batch
+    idx.search(torch.empty((0, w.d), device="cuda"), torch.empty(0, device="cuda"), k=5, ef=20)
+    torch.cuda.synchronize()
+    assert idx.device_status() == 0
+    idx.close()
+
+
+def test_tiny_graph_fewer_points_than_k(U):
+    base = np.array([[0.0] * 8, [1.0] * 8, [3.0] * 8], np.float32)
+    g = oracle.hnsw_build(base, 1, 2, 4, np.zeros(3, np.int32))
+    g2 = oracle.hnsw_build(base, 2, 2, 4, np.zeros(3, np.int32))
+    idx = U.Index(base, g, g2)
+    q = np.array([[0.9] * 8], np.float32)
+    ids, dist, _ = idx.search(dev(q), dev(np.array([0.7], np.float32)), k=5, ef=8)
+    assert ids.cpu().numpy().tolist() == [[1, 0, 2, -1, -1]]
+    assert np.isinf(dist.cpu().numpy()[0, 3:]).all()
+    idx.close()

@@ -1,0 +1,140 @@
+"""Host-side checks of libuhnsw.so (no GPU): it builds, exports every entry
+point of include/uhnsw.h, validates arguments before touching the device, and
+its host graph builder matches the oracle's construction."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_02030_gb300 import _build, inputs as I
+from paper_2605_02030_gb300 import uhnsw as U
+
+from helpers import workload_arrays
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def lib():
+    _build.build()
+    return U.load_library()
+
+
+def test_exports_every_declared_symbol(lib):
+    hdr = open(os.path.join(ROOT, "include", "uhnsw.h")).read()
+    declared = set(re.findall(r"\b(uhnsw_[a-z_]+)\s*\(", hdr))
+    assert declared == set(U.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+    out = os.popen(f"nm -D --defined-only {_build.LIB}").read()
+    for name in declared:
+        assert re.search(rf"\bT {name}\b", out), f"{name} not exported"
+
+
+def test_load_validation_errors(lib):
+    base = np.zeros((4, 8), np.float32)
+    h = C.c_void_p(0)
+    assert lib.uhnsw_load(None, 4, 8, None, None, None, C.byref(h)) == -1
+    assert b"base" in lib.uhnsw_last_error()
+    g = {"num_levels": 1, "entry_point": 0, "max_degree0": 2, "max_degree": 2, "n": 4,
+         "levels": [{"nodes": np.arange(4, dtype=np.int32), "offsets": np.array([0, 1, 2, 3, 4]),
+                     "nbrs": np.array([1, 0, 3, 9], np.int32)}]}          # 9 is out of range
+    s, keep = U._graph_struct(g)
+    assert lib.uhnsw_load(base.ctypes.data, 4, 8, C.byref(s), None, None, C.byref(h)) == -1
+    assert b"out of range" in lib.uhnsw_last_error()
+    g["levels"][0]["nbrs"] = np.array([1, 0, 3, 2], np.int32)
+    g["entry_point"] = 7
+    s, keep = U._graph_struct(g)
+    assert lib.uhnsw_load(base.ctypes.data, 4, 8, C.byref(s), None, None, C.byref(h)) == -1
+    assert b"entry point" in lib.uhnsw_last_error()
+    g["entry_point"] = 0
+    g["max_degree0"] = 0
+    s, keep = U._graph_struct(g)
+    assert lib.uhnsw_load(base.ctypes.data, 4, 8, C.byref(s), None, None, C.byref(h)) == -1
+    assert lib.uhnsw_load(base.ctypes.data, 4, 0, C.byref(s), None, None, C.byref(h)) == -1
+    assert lib.uhnsw_load(base.ctypes.data, 4, 8, None, None, None, C.byref(h)) == -1
+    # an upper level listing a node that is not on the level below
+    g = {"num_levels": 2, "entry_point": 3, "max_degree0": 2, "max_degree": 2, "n": 4,
+         "levels": [{"nodes": np.arange(4, dtype=np.int32), "offsets": np.array([0, 1, 2, 3, 4]),
+                     "nbrs": np.array([1, 0, 3, 2], np.int32)},
+                    {"nodes": np.array([3, 2], np.int32), "offsets": np.array([0, 0, 0]),
+                     "nbrs": np.zeros(0, np.int32)}]}
+    s, keep = U._graph_struct(g)
+    assert lib.uhnsw_load(base.ctypes.data, 4, 8, C.byref(s), None, None, C.byref(h)) == -1
+    assert b"ascending" in lib.uhnsw_last_error()
+
+
+def test_search_validation_errors(lib):
+    assert lib.uhnsw_search(None, None, None, None, None, 1, 10, 64, None, None, None, None) == -1
+    assert lib.uhnsw_verify(None, None, None, None, 1, 1, 1, None, None, None, None) == -1
+    assert lib.uhnsw_exact(None, None, None, 1, 1, None, None, None) == -1
+    assert lib.uhnsw_index_info(None, None, None, None, None, None) == -1
+
+
+def test_build_graph_validation(lib):
+    base = np.zeros((10, 4), np.float32)
+    lv = np.zeros(10, np.int32)
+    h = C.c_void_p(0)
+    assert lib.uhnsw_build_graph(base.ctypes.data, 10, 4, 3, 4, 10, lv.ctypes.data, 1, C.byref(h)) == -1
+    assert lib.uhnsw_build_graph(base.ctypes.data, 10, 4, 1, 1, 10, lv.ctypes.data, 1, C.byref(h)) == -1
+    lv[3] = -2
+    assert lib.uhnsw_build_graph(base.ctypes.data, 10, 4, 1, 4, 10, lv.ctypes.data, 1, C.byref(h)) == -1
+
+
+def _same_graph(a, b):
+    if a["num_levels"] != b["num_levels"] or a["entry_point"] != b["entry_point"]:
+        return False
+    for x, y in zip(a["levels"], b["levels"]):
+        for key in ("nodes", "offsets", "nbrs"):
+            if not np.array_equal(x[key], y[key]):
+                return False
+    return True
+
+
+@pytest.mark.parametrize("case", [("sift1m", 3000, 0.0, dict(M=8, ef_construction=40)),
+                                  ("mixture10k", 3000, 1 / 16, dict(M=8, ef_construction=30))])
+def test_builder_single_thread_equals_oracle(lib, case):
+    """Integer data (and data on a 1/16 grid) make FP32 L1/L2 sums exact, so
+    one-thread insertion reproduces the oracle's FP64 construction exactly."""
+    name, n, grid, kw = case
+    w, base, *_ = workload_arrays(name, n, 4, grid, **kw)
+    for metric in (1, 2):
+        lv = I.graph_levels(w, metric)
+        go = oracle.hnsw_build(base, metric, w.M, w.ef_construction, lv)
+        gp = U.build_graph(base, metric, w.M, w.ef_construction, lv, threads=1)
+        assert _same_graph(go, gp), (name, metric)
+
+
+def test_builder_parallel_invariants(lib):
+    w, base, *_ = workload_arrays("sift1m", 8000, 4, 0.0, M=12, ef_construction=60)
+    lv = I.graph_levels(w, 2)
+    g = U.build_graph(base, 2, w.M, w.ef_construction, lv, threads=4)
+    assert g["num_levels"] == lv.max() + 1 and lv[g["entry_point"]] == lv.max()
+    for l, L in enumerate(g["levels"]):
+        np.testing.assert_array_equal(L["nodes"], np.nonzero(lv >= l)[0])
+        deg = np.diff(L["offsets"])
+        assert deg.max() <= (2 * w.M if l == 0 else w.M)
+        assert (lv[L["nbrs"]] >= l).all()
+    # Pruned reverse links leave a few nodes without an in-link on layer 0 in
+    # any HNSW build (the oracle's too), so reachability from the entry point
+    # is compared with the single-threaded build rather than required to be 1.
+    def reach(gr):
+        L0 = gr["levels"][0]
+        seen = np.zeros(w.n, bool)
+        seen[gr["entry_point"]] = True
+        fr = [gr["entry_point"]]
+        while fr:
+            nxt = []
+            for v in fr:
+                for u in L0["nbrs"][L0["offsets"][v]:L0["offsets"][v + 1]]:
+                    if not seen[u]:
+                        seen[u] = True
+                        nxt.append(int(u))
+            fr = nxt
+        return seen.mean()
+
+    g1 = U.build_graph(base, 2, w.M, w.ef_construction, lv, threads=1)
+    assert reach(g) >= reach(g1) - 0.01
