@@ -1,0 +1,465 @@
+#!/usr/bin/env python
+"""QPS at recall@10 >= 0.95 for U-HNSW queries with mixed p on the 1M x 128
+SIFT-shaped workload: the plain FP32 form (one block per query, FP32 rows)
+against the FP16 batched form (FP16 traversal rows, persistent launch over a
+device work queue, replayed as a CUDA graph).
+
+One step = one pass of the whole query path (routing, HNSW search on G1/G2,
+L_p verification, output) over the batch of 10,000 queries, inputs resident
+in HBM.  The operating point of each form is the smallest ef whose recall@10
+reaches 0.95 in every p bin.  Between timed steps the L2 cache is flushed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (plain single-threaded FP64 restatement
+of Algorithm 1) on the same graphs and queries.  With torchrun (N > 1) every
+rank holds a replica and answers its own batch (weak scaling, no collective on
+the data path); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2605_02030_gb300 import inputs as I  # noqa: E402
+
+METRIC = ("QPS at recall@10>=0.95, mixed p in (0.5,2], 1M×128; plain FP32 vs FP16 batched")
+UNIT = "queries/s"
+EF_SWEEP = (16, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512)
+RECALL_TARGET = 0.95
+CACHE = os.environ.get("UHNSW_CACHE", os.path.join(ROOT, ".uhnsw_cache"))
+
+
+# ---------------------------------------------------------------- distributed helpers
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def reduce_max(x: float, world: int) -> float:
+    """Max over ranks (host value); identity for one process."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def aggregate_value(units_per_rank: int, world: int, seconds_max: float) -> float:
+    """Whole-job throughput: units processed by all ranks / the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
+# ---------------------------------------------------------------- inputs, graphs, ground truth
+def _key(*parts) -> str:
+    return hashlib.sha1(repr(parts).encode()).hexdigest()[:16]
+
+
+def workload(args) -> I.Workload:
+    w = I.WORKLOADS["sift1m"]
+    if args.n:
+        w = w.scaled(n=args.n)
+    if args.nq:
+        w = w.scaled(nq=args.nq)
+    return w
+
+
+def save_graph(path, g):
+    arrs = {"meta": np.array([g["num_levels"], g["entry_point"], g["max_degree0"],
+                              g["max_degree"], g["n"]], np.int64)}
+    for l, lv in enumerate(g["levels"]):
+        arrs[f"n{l}"], arrs[f"o{l}"], arrs[f"e{l}"] = lv["nodes"], lv["offsets"], lv["nbrs"]
+    tmp = path + f".{os.getpid()}.tmp.npz"
+    np.savez(tmp, **arrs)
+    os.replace(tmp, path)
+
+
+def load_graph(path):
+    z = np.load(path)
+    L, ep, m0, m, n = (int(v) for v in z["meta"])
+    return {"num_levels": L, "entry_point": ep, "max_degree0": m0, "max_degree": m, "n": n,
+            "levels": [{"nodes": z[f"n{l}"], "offsets": z[f"o{l}"], "nbrs": z[f"e{l}"]}
+                       for l in range(L)]}
+
+
+def graphs_for(w: I.Workload, base: np.ndarray, log):
+    """G1 (L1) and G2 (L2) built by the library's multi-threaded HNSW insertion
+    (Section 2.2), cached on disk keyed by the workload recipe."""
+    os.makedirs(CACHE, exist_ok=True)
+    out = []
+    for metric in (1, 2):
+        path = os.path.join(CACHE, f"graph_{w.name}_{_key(w.n, w.d, w.seed, w.M, w.ef_construction, metric)}.npz")
+        if os.path.exists(path):
+            out.append(load_graph(path))
+            continue
+        from paper_2605_02030_gb300 import uhnsw as U
+        t0 = time.time()
+        g = U.build_graph(base, metric, w.M, w.ef_construction, I.graph_levels(w, metric), threads=0)
+        log(f"built G{metric} in {time.time() - t0:.1f} s")
+        save_graph(path, g)
+        out.append(g)
+    return out
+
+
+def ground_truth(w, idx, q_dev, p_dev, k, log):
+    import torch
+    path = os.path.join(CACHE, f"gt_{w.name}_{_key(w.n, w.d, w.seed, w.nq, k)}.npy")
+    if os.path.exists(path):
+        return np.load(path)
+    t0 = time.time()
+    ids, _ = idx.exact(q_dev, p_dev, k)
+    torch.cuda.synchronize()
+    gt = ids.cpu().numpy()
+    log(f"exact ground truth on the GPU in {time.time() - t0:.1f} s")
+    np.save(path, gt)
+    return gt
+
+
+def recall_per_bin(ids, gt, p, k=10):
+    hits = np.array([len(set(a[:k].tolist()) & set(b[:k].tolist())) / k for a, b in zip(ids, gt)])
+    bins = np.clip(np.floor((p - 0.5) / 0.1 + 1e-6).astype(int), 0, 15)
+    per = {int(b): float(hits[bins == b].mean()) for b in np.unique(bins)}
+    return float(hits.mean()), per
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.dev), "-lms", "50"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, log):
+    import torch
+    import paper_2605_02030_gb300 as pkg
+    from paper_2605_02030_gb300 import uhnsw as U
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local_rank)
+    pkg.build()
+    w = workload(args)
+    t0 = time.time()
+    base = I.base_vectors(w)
+    qs = I.query_vectors(w)
+    p, _, _ = I.query_params(w)
+    log(f"inputs {w.n}x{w.d}, {w.nq} queries in {time.time() - t0:.1f} s")
+    g1, g2 = graphs_for(w, base, log)
+    k = 10
+    q_dev = torch.from_numpy(qs).cuda()
+    p_dev = torch.from_numpy(p).cuda()
+    stream = torch.cuda.Stream()
+    idx32 = U.Index(base, g1, g2, traverse_dtype="f32")
+    idx16 = U.Index(base, g1, g2, traverse_dtype="f16")
+    gt = ground_truth(w, idx32, q_dev, p_dev, k, log)
+
+    forms = {
+        "plain_fp32": dict(index=idx32, opts=dict()),
+        "fp16_batched": dict(index=idx16, opts=dict(persistent=True, use_graph=True)),
+    }
+    # calibration (untimed): smallest ef meeting the recall target in every p bin
+    for name, f in forms.items():
+        f["ef"], f["recall"], f["recall_min_bin"] = None, None, None
+        for ef in EF_SWEEP:
+            with torch.cuda.stream(stream):
+                ids, _, _ = f["index"].search(q_dev, p_dev, k=k, ef=ef, stream=stream, **f["opts"])
+            torch.cuda.synchronize()
+            r, per = recall_per_bin(ids.cpu().numpy(), gt, p, k)
+            f["ef"], f["recall"], f["recall_min_bin"] = ef, r, min(per.values())
+            if min(per.values()) >= RECALL_TARGET:
+                break
+        log(f"{name}: ef={f['ef']} recall={f['recall']:.4f} min-bin={f['recall_min_bin']:.4f}")
+
+    flush = torch.empty(384 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out_ids = torch.empty((w.nq, k), dtype=torch.int64, device="cuda")
+    out_d = torch.empty((w.nq, k), dtype=torch.float32, device="cuda")
+
+    def time_form(f, steps, warmup):
+        call = lambda: f["index"].search(q_dev, p_dev, k=k, ef=f["ef"], stream=stream,
+                                         out=(out_ids, out_d), **f["opts"])
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                call()
+        torch.cuda.synchronize()
+        barrier(world)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        with torch.cuda.stream(stream):
+            for a, b in evs:
+                flush.fill_(1.0)              # L2 flush, outside the timed region
+                a.record(stream)
+                call()
+                b.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return [a.elapsed_time(b) for a, b in evs]
+
+    for name, f in forms.items():
+        f["ms"] = time_form(f, max(5, args.steps // 2), args.warmup)
+    head = forms["fp16_batched"]
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        head["ms"] = time_form(head, args.steps, args.warmup)
+    clocks = clk.summary()
+    total_s = sum(head["ms"]) / 1e3
+    total_s_max = reduce_max(total_s, world)
+    value = aggregate_value(args.steps * w.nq, world, total_s_max)
+
+    # algorithmic bytes of one launch (counted by the kernel's own counters)
+    _, _, st = head["index"].search(q_dev, p_dev, k=k, ef=head["ef"], stats=True)
+    st = st.cpu().numpy().astype(np.int64)
+    row16, row32 = w.d * 2, w.d * 4
+    deg0 = g1["max_degree0"]
+    alg_bytes = int((st[:, 0] * row16).sum() + (st[:, 7] * deg0 * 4).sum() + (st[:, 2] * 4).sum()
+                    + w.nq * (w.d * 4 + 4 + k * 12))
+    kern_s = statistics.mean(head["ms"]) / 1e3
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = alg_bytes / kern_s / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "search_kernel_traffic.json")
+    if os.path.exists(prof):
+        try:
+            pj = json.load(open(prof))
+            if pj.get("source_sha") == _source_sha():
+                traffic = pj.get("dram_bytes_per_launch")
+        except (OSError, ValueError):
+            pass
+
+    # end to end through the public C ABI with host buffers (copies inside the timed region)
+    pin_q = torch.from_numpy(qs).pin_memory().numpy()
+    pin_p = torch.from_numpy(p).pin_memory().numpy()
+    pin_ids = torch.empty((w.nq, k), dtype=torch.int64).pin_memory().numpy()
+    pin_d = torch.empty((w.nq, k), dtype=torch.float32).pin_memory().numpy()
+    e2e_opts = dict(persistent=True)
+    for _ in range(args.warmup):
+        head["index"].search_host(pin_q, pin_p, k=k, ef=head["ef"], out=(pin_ids, pin_d),
+                                  stream=stream, **e2e_opts)
+    e2e_t = []
+    for _ in range(max(5, args.steps // 2)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        head["index"].search_host(pin_q, pin_p, k=k, ef=head["ef"], out=(pin_ids, pin_d),
+                                  stream=stream, **e2e_opts)
+        e2e_t.append(time.perf_counter() - t1)
+    e2e_max = reduce_max(sum(e2e_t), world)
+    e2e_val = aggregate_value(len(e2e_t) * w.nq, world, e2e_max)
+    e2e_recall, _ = recall_per_bin(pin_ids, gt, p, k)
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(statistics.mean(head["ms"]), 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": f"sift1m: N={w.n:,} d={w.d} integer 0..255, {w.n_clusters} clustered "
+                        f"Gaussians; {w.nq:,} queries, p on the grid 0.5..2.0; k={k}; "
+                        f"G1/G2 M={w.M} efConstruction={w.ef_construction}",
+            "form": "fp16_batched: FP16 traversal rows, FP32 verification, persistent launch, "
+                    "CUDA-graph replay",
+            "ef": head["ef"], "t": "ef", "verify": "exact with partial-sum abandon",
+            "recall_at_10": round(head["recall"], 4),
+            "recall_at_10_min_p_bin": round(head["recall_min_bin"], 4),
+            "l2": "flushed (384 MB write) between timed steps",
+            "plain_fp32": {"value": round(args.steps and 1e3 * w.nq / statistics.mean(
+                forms["plain_fp32"]["ms"]), 1), "ef": forms["plain_fp32"]["ef"],
+                "recall_at_10": round(forms["plain_fp32"]["recall"], 4),
+                "recall_at_10_min_p_bin": round(forms["plain_fp32"]["recall_min_bin"], 4),
+                "ms_per_step": round(statistics.mean(forms["plain_fp32"]["ms"]), 4)},
+            "stats_per_query": {"N_b": float(st[:, 0].mean()), "N_p": float(st[:, 1].mean()),
+                                "lp_terms": float(st[:, 2].mean()),
+                                "expansions": float(st[:, 3].mean())},
+        },
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+        "e2e": {"value": round(e2e_val, 1), "unit": UNIT,
+                "h2d_bytes_per_step": int(qs.nbytes + p.nbytes),
+                "d2h_bytes_per_step": int(w.nq * k * 12), "recall_at_10": round(e2e_recall, 4),
+                "api": "uhnsw_search_host (pinned host buffers)"},
+        "clocks": clocks,
+        "gpu_launches": args.steps,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, base, qs, p, g1, g2, head["ef"], k, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    idx32.close()
+    idx16.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _source_sha() -> str:
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2605_02030_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------- oracle arm
+def cpu_baseline(w, base, qs, p, g1, g2, ef, k, seconds):
+    """The oracle (single-threaded FP64 Algorithm 1) on a time-bounded sample of
+    the same queries, on this host's cores."""
+    import oracle
+    oracle.build()
+    holders = (oracle._CSRHolder(g1), oracle._CSRHolder(g2))
+    n_done = 0
+    t0 = time.perf_counter()
+    while n_done < len(qs) and time.perf_counter() - t0 < seconds:
+        oracle.uhnsw_query(g1, g2, base, qs[n_done], float(p[n_done]), k, ef, _holders=holders)
+        n_done += 1
+    dt = time.perf_counter() - t0
+    return {"value": round(n_done / dt, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n_done} of the {len(qs)} queries at ef={ef} ({dt:.1f} s, "
+                      f"single thread, FP64)"}
+
+
+def run_reference(args, log):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    w = workload(args)
+    base = I.base_vectors(w)
+    qs = I.query_vectors(w)
+    p, _, _ = I.query_params(w)
+    g1, g2 = graphs_for(w, base, log)
+    import oracle
+    oracle.build()
+    holders = (oracle._CSRHolder(g1), oracle._CSRHolder(g2))
+    ef, k = args.ref_ef, 10
+    per_step = max(1, int(args.ref_queries_per_step))
+
+    def step(off):
+        for j in range(per_step):
+            i = (off + j) % len(qs)
+            oracle.uhnsw_query(g1, g2, base, qs[i], float(p[i]), k, ef, _holders=holders)
+
+    for s in range(args.warmup):
+        step(s * per_step)
+    t = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        step((args.warmup + s) * per_step)
+        t.append(time.perf_counter() - t0)
+    value = per_step * len(t) / sum(t)
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * statistics.mean(t), 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": f"sift1m: N={w.n:,} d={w.d}; each step {per_step} of the "
+                               f"{w.nq:,} queries at ef={ef}, k={k}",
+                   "form": "CPU oracle: plain single-threaded FP64 Algorithm 1"},
+        "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} queries per step"},
+        "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=0, help="base size override (smaller runs)")
+    ap.add_argument("--nq", type=int, default=0, help="queries per step override")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-ef", type=int, default=128)
+    ap.add_argument("--ref-queries-per-step", type=int, default=100)
+    ap.add_argument("--quiet", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    def log(msg):
+        if not args.quiet and dist_env()[0] == 0:
+            print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+    if args.impl == "reference":
+        run_reference(args, log)
+    else:
+        run_ours(args, log)
+
+
+if __name__ == "__main__":
+    main()

@@ -104,7 +104,8 @@ enum {
 typedef struct {
   int32_t t;             /* |C|, candidates verified; 0 => ef (the whole beam); raised to k */
   int32_t kappa;         /* batch size of Algorithm 1; 0 => k */
-  float tau;             /* early-termination threshold of Algorithm 1; 0 => 0.92 */
+  float tau;             /* early-termination threshold of Algorithm 1; 0 => 0.92;
+                            a negative value stops after the first batch */
   float cutoff;          /* routing: p <= cutoff searches G1; 0 => 1.4 */
   int32_t verify_mode;   /* uhnsw_verify_mode */
   int32_t search_width;  /* beam entries expanded per step; <= 1 => exactly HNSW's order */

@@ -340,7 +340,7 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   if (o) opts = *o;
   if (opts.t < 0 || opts.t > UHNSW_MAX_EF) return fail(UHNSW_EINVAL, "uhnsw_search: t=%d", opts.t);
   if (opts.kappa < 0) return fail(UHNSW_EINVAL, "uhnsw_search: kappa=%d", opts.kappa);
-  if (!(opts.tau >= 0.f) || !std::isfinite(opts.tau)) return fail(UHNSW_EINVAL, "uhnsw_search: tau");
+  if (!std::isfinite(opts.tau)) return fail(UHNSW_EINVAL, "uhnsw_search: tau");
   if (!(opts.cutoff >= 0.f) || !std::isfinite(opts.cutoff))
     return fail(UHNSW_EINVAL, "uhnsw_search: cutoff");
   if (opts.verify_mode != UHNSW_VERIFY_EXACT && opts.verify_mode != UHNSW_VERIFY_PAPER)
@@ -392,7 +392,7 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   a.ef_cap = ef_cap;
   a.t = opts.t;
   a.kappa = opts.kappa;
-  a.tau = opts.tau > 0.f ? opts.tau : 0.92f;
+  a.tau = opts.tau != 0.f ? opts.tau : 0.92f;
   a.cutoff = opts.cutoff > 0.f ? opts.cutoff : 1.4f;
   a.mode = opts.verify_mode;
   a.width = width;
@@ -554,7 +554,7 @@ extern "C" int uhnsw_verify(uhnsw_index* idx, const float* q, const float* p, co
   if (o) opts = *o;
   if (opts.verify_mode != UHNSW_VERIFY_EXACT && opts.verify_mode != UHNSW_VERIFY_PAPER)
     return fail(UHNSW_EINVAL, "uhnsw_verify: verify_mode");
-  if (opts.kappa < 0 || !(opts.tau >= 0.f)) return fail(UHNSW_EINVAL, "uhnsw_verify: kappa/tau");
+  if (opts.kappa < 0 || !std::isfinite(opts.tau)) return fail(UHNSW_EINVAL, "uhnsw_verify: kappa/tau");
   if (nq == 0) return UHNSW_OK;
   QueryArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -567,7 +567,7 @@ extern "C" int uhnsw_verify(uhnsw_index* idx, const float* q, const float* p, co
   a.nq = nq;
   a.k_max = k;
   a.kappa = opts.kappa;
-  a.tau = opts.tau > 0.f ? opts.tau : 0.92f;
+  a.tau = opts.tau != 0.f ? opts.tau : 0.92f;
   a.mode = opts.verify_mode;
   a.cmax = kBlock / 8;
   a.vcap = std::max(t, 1);
