@@ -15,6 +15,10 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libuhnsw.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
+# UHNSW_CHECK=1 builds the diagnostic variant whose kernels record (and clamp)
+# any out-of-range index instead of accessing it.
+CHECK = os.environ.get("UHNSW_CHECK", "0") == "1"
+EXTRA = ["-DUHNSW_CHECK"] if CHECK else []
 
 
 def _sources():
@@ -28,7 +32,7 @@ def _compile(src: str) -> str:
     obj = os.path.join(OUT_DIR, src.rsplit(".", 1)[0] + ".o")
     path = os.path.join(CSRC, src)
     if src.endswith(".cu"):
-        cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+        cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *EXTRA,
                f"-I{INC}", f"-I{CSRC}", "-c", path, "-o", obj]
     else:
         cmd = ["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", f"-I{INC}", f"-I{CSRC}",
@@ -43,7 +47,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     cu, cpp, deps = _sources()
     newest = max(os.path.getmtime(p) for p in deps)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
+    stamp = LIB + ".flags"
+    flags = " ".join(EXTRA)
+    same_flags = os.path.exists(stamp) and open(stamp).read() == flags
+    if not force and same_flags and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
     srcs = cu + cpp
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
@@ -54,6 +61,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(flags)
     if verbose:
         print(LIB)
     return LIB

@@ -44,6 +44,7 @@ struct DevGraph {
   int32_t* ell0 = nullptr;
   int32_t* up_row = nullptr;
   int32_t* up_adj = nullptr;
+  int32_t up_rows = 0;
   int32_t entry = 0, top_level = 0, deg0 = 0, deg = 0;
   int64_t bytes = 0;
 };
@@ -210,6 +211,7 @@ GraphDev to_dev(const DevGraph& g) {
   r.ell0 = g.present ? g.ell0 : nullptr;
   r.up_row = g.up_row;
   r.up_adj = g.up_adj;
+  r.up_rows = g.up_rows;
   r.entry = g.entry;
   r.top_level = g.top_level;
   r.deg0 = g.deg0;
@@ -294,14 +296,15 @@ extern "C" int uhnsw_load(const float* base, int64_t n, int32_t d, const uhnsw_g
       G.top_level = gs[i]->num_levels - 1;
       G.deg0 = gs[i]->max_degree0;
       G.deg = gs[i]->max_degree;
+      G.up_rows = (int32_t)(upa[i].size() / G.deg);
       rc = upload(ell[i], &G.ell0, &idx->bytes);
       if (rc == UHNSW_OK) rc = upload(upr[i], &G.up_row, &idx->bytes);
       if (rc == UHNSW_OK) rc = upload(upa[i], &G.up_adj, &idx->bytes);
     }
     if (rc != UHNSW_OK) break;
-    e = cudaMalloc(&idx->err, 4);
+    e = cudaMalloc(&idx->err, 16);
     if (e == cudaSuccess) e = cudaMalloc(&idx->queue_head, 64);
-    if (e == cudaSuccess) e = cudaMemset(idx->err, 0, 4);
+    if (e == cudaSuccess) e = cudaMemset(idx->err, 0, 16);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&idx->capture_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) { rc = cuda_fail(e, "uhnsw_load: state"); break; }
   } while (0);
@@ -627,11 +630,13 @@ extern "C" int uhnsw_device_status(uhnsw_index* idx) {
   if (!idx) return fail(UHNSW_EINVAL, "uhnsw_device_status: index is NULL");
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "uhnsw_device_status: synchronize");
-  int32_t v = 0;
-  e = cudaMemcpy(&v, idx->err, 4, cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess) e = cudaMemset(idx->err, 0, 4);
+  int32_t v[4] = {0, 0, 0, 0};
+  e = cudaMemcpy(v, idx->err, 16, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(idx->err, 0, 16);
   if (e != cudaSuccess) return cuda_fail(e, "uhnsw_device_status: read");
-  if (v != 0) return fail(v, "uhnsw_device_status: device recorded error %d", v);
+  if (v[0] != 0)
+    return fail(v[0], "uhnsw_device_status: device recorded error %d (site %d, value %d, limit %d)",
+                v[0], v[1], v[2], v[3]);
   return UHNSW_OK;
 }
 

@@ -107,9 +107,32 @@ __device__ __forceinline__ float pow_term(float a, float p) {
   return hw_ex2(p * hw_lg2(a));
 }
 
-// Records the first error code of a launch into the sticky device word.
+// Records the first error code of a launch into the sticky device word
+// (err[0]; err[1..3] hold the site, value and limit of a failed index check).
 __device__ __forceinline__ void set_error(int32_t* err, int32_t code) {
   if (err) atomicCAS(err, 0, code);
+}
+
+// Index check of the diagnostic build (compiled with -DUHNSW_CHECK): an index
+// outside [0, limit) is recorded (code UHNSW_ECAPACITY, site, value, limit)
+// and replaced by 0 so that the access stays inside the buffer.  In the
+// normal build it is the identity.
+__device__ __forceinline__ int64_t chk_idx(int64_t i, int64_t limit, int site, int32_t* err) {
+#ifdef UHNSW_CHECK
+  if (i < 0 || i >= limit) {
+    if (err && atomicCAS(err, 0, UHNSW_ECAPACITY) == 0) {
+      err[1] = site;
+      err[2] = (int32_t)i;
+      err[3] = (int32_t)limit;
+    }
+    return 0;
+  }
+#else
+  (void)limit;
+  (void)site;
+  (void)err;
+#endif
+  return i;
 }
 
 __device__ __forceinline__ uint32_t hash_slot(int32_t id, int bits) {
@@ -160,6 +183,7 @@ __device__ __forceinline__ int block_merge(const float* ld, const uint32_t* li, 
     int32_t xi = (int32_t)(ni[i] & kIdMask);
     int r = 0;
     for (int j = 0; j < m; ++j) r += pair_lt(nd[j], (int32_t)(ni[j] & kIdMask), x, xi);
+    r = (int)chk_idx(r, m, 8, nullptr);
     sd[r] = x;
     si[r] = ni[i];
   }

@@ -42,6 +42,7 @@ struct GraphDev {
   const int32_t* ell0;   // [n][deg0] layer-0 links, -1 padded
   const int32_t* up_row; // [n] first upper-level row of the node, -1 if it is only on layer 0
   const int32_t* up_adj; // [rows][deg], -1 padded; row of (v, level l) = up_row[v] + l - 1
+  int32_t up_rows;
   int32_t entry;
   int32_t top_level;
   int32_t deg0;
@@ -124,6 +125,12 @@ struct BlockScalars {
   int ri[32];
 };
 
+__device__ __forceinline__ uint32_t dynamic_smem_bytes() {
+  uint32_t r;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+  return r;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned r;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
@@ -166,7 +173,8 @@ __device__ __forceinline__ void block_argmin(const float* d, const uint32_t* id,
 template <typename T, int TEAM, int CPL, int BLOCK, int METRIC>
 __device__ __forceinline__ void dist_batch(const T* __restrict__ rows, int d_pad,
                                            const float (&qv)[CPL][Elems16<T>::n],
-                                           const uint32_t* ids, float* out, int m) {
+                                           const uint32_t* ids, float* out, int m, int64_t n,
+                                           int32_t* err) {
   constexpr int VEC = Elems16<T>::n;
   constexpr int NT = BLOCK / TEAM;
   constexpr int U = 2;
@@ -179,8 +187,8 @@ __device__ __forceinline__ void dist_batch(const T* __restrict__ rows, int d_pad
     for (int u = 0; u < U; ++u) {
       const int i = r * NT * U + u * NT + team;
       const bool ok = i < m;
-      const uint4* row =
-          reinterpret_cast<const uint4*>(rows + (ok ? (int64_t)(ids[i] & kIdMask) * d_pad : 0));
+      const int64_t id = ok ? chk_idx((int64_t)(ids[i] & kIdMask), n, 1, err) : 0;
+      const uint4* row = reinterpret_cast<const uint4*>(rows + id * d_pad);
 #pragma unroll
       for (int c = 0; c < CPL; ++c) {
         const int ch = lane + c * TEAM;
@@ -212,9 +220,10 @@ __device__ __forceinline__ void dist_batch(const T* __restrict__ rows, int d_pad
 template <typename T, int TEAM, int CPL, int BLOCK>
 __device__ __forceinline__ void dist_batch_metric(int metric, const T* rows, int d_pad,
                                                   const float (&qv)[CPL][Elems16<T>::n],
-                                                  const uint32_t* ids, float* out, int m) {
-  if (metric == 1) dist_batch<T, TEAM, CPL, BLOCK, 1>(rows, d_pad, qv, ids, out, m);
-  else dist_batch<T, TEAM, CPL, BLOCK, 2>(rows, d_pad, qv, ids, out, m);
+                                                  const uint32_t* ids, float* out, int m,
+                                                  int64_t n, int32_t* err) {
+  if (metric == 1) dist_batch<T, TEAM, CPL, BLOCK, 1>(rows, d_pad, qv, ids, out, m, n, err);
+  else dist_batch<T, TEAM, CPL, BLOCK, 2>(rows, d_pad, qv, ids, out, m, n, err);
 }
 
 // ---------------------------------------------------------------- verification
@@ -273,7 +282,7 @@ __device__ __forceinline__ void verify_wave(const QueryArgs& a, const float* qs,
   const unsigned tmask = 0xffu << ((threadIdx.x & 31) & ~7);
   const int i = w0 + team;
   if (i < wend) {
-    const int32_t id = (int32_t)(C[i] & kIdMask);
+    const int32_t id = (int32_t)chk_idx((int64_t)(C[i] & kIdMask), a.n, 2, a.err);
     float S = 0.f;
     int groups = 0;
     const bool done = lp_sum_team<PM>(a.base32, a.d, a.d_pad, qs, p, id, thr, tmask, lane8, S,
@@ -282,7 +291,7 @@ __device__ __forceinline__ void verify_wave(const QueryArgs& a, const float* qs,
       atomicAdd(&s.np, 1);
       atomicAdd(&s.terms, min(groups * 32, a.d));
       if (done) {
-        const int pos = atomicAdd(&s.wm, 1);
+        const int pos = (int)chk_idx(atomicAdd(&s.wm, 1), BLOCK / 8, 9, a.err);
         vb.wd[pos] = S;
         vb.wi[pos] = (uint32_t)id;
       }
@@ -418,12 +427,13 @@ __device__ __forceinline__ void write_invalid(const QueryArgs& a, int64_t qi, in
 
 // Ballot compaction of `keep` lanes' values into out[s.m ...] (order within a
 // warp kept, across warps arbitrary).
-__device__ __forceinline__ void compact_append(bool keep, uint32_t v, uint32_t* out, int* counter) {
+__device__ __forceinline__ void compact_append(bool keep, uint32_t v, uint32_t* out, int* counter,
+                                               int cap, int32_t* err) {
   const unsigned ball = __ballot_sync(kFull, keep);
   int base = 0;
   if ((threadIdx.x & 31) == 0 && ball) base = atomicAdd(counter, __popc(ball));
   base = __shfl_sync(kFull, base, 0);
-  if (keep) out[base + __popc(ball & lanemask_lt())] = v;
+  if (keep) out[chk_idx(base + __popc(ball & lanemask_lt()), cap, 6, err)] = v;
 }
 
 // ---------------------------------------------------------------- one query
@@ -478,7 +488,7 @@ __device__ void run_query(const QueryArgs& a, int64_t qi, unsigned char* smem, c
   // 2. greedy descent through the upper levels (HNSW search with beam 1)
   if (tid == 0) ci[0] = (uint32_t)g.entry;
   __syncthreads();
-  dist_batch_metric<T, TEAM, CPL, BLOCK>(metric, trav, a.d_pad, qv, ci, cd, 1);
+  dist_batch_metric<T, TEAM, CPL, BLOCK>(metric, trav, a.d_pad, qv, ci, cd, 1, a.n, a.err);
   __syncthreads();
   int cur = g.entry;
   float cur_d = cd[0];
@@ -488,22 +498,22 @@ __device__ void run_query(const QueryArgs& a, int64_t qi, unsigned char* smem, c
     for (int guard = 0; guard <= (int)min(a.n, (int64_t)INT_MAX - 1); ++guard) {
       if (tid == 0) s.m = 0;
       __syncthreads();
-      const int32_t row = g.up_row[cur];
+      const int32_t row = g.up_row[chk_idx(cur, a.n, 3, a.err)];
       if (row < 0) {
         set_error(a.err, UHNSW_EINVAL);
         break;
       }
-      const int32_t* adj = g.up_adj + ((int64_t)row + l - 1) * g.deg;
+      const int32_t* adj = g.up_adj + chk_idx((int64_t)row + l - 1, g.up_rows, 4, a.err) * g.deg;
       for (int b0 = 0; b0 < g.deg; b0 += BLOCK) {
         const int j = b0 + tid;
         const int32_t v = j < g.deg ? adj[j] : -1;
-        compact_append(v >= 0, (uint32_t)v, ci, &s.m);
+        compact_append(v >= 0, (uint32_t)v, ci, &s.m, a.cmax, a.err);
       }
       __syncthreads();
       const int m = s.m;
       nadj += 1;
       nb += m;
-      dist_batch_metric<T, TEAM, CPL, BLOCK>(metric, trav, a.d_pad, qv, ci, cd, m);
+      dist_batch_metric<T, TEAM, CPL, BLOCK>(metric, trav, a.d_pad, qv, ci, cd, m, a.n, a.err);
       __syncthreads();
       block_argmin<BLOCK>(cd, ci, m, s);
       if (m > 0 && pair_lt(s.bestd, s.besti, cur_d, cur)) {
@@ -534,7 +544,10 @@ __device__ void run_query(const QueryArgs& a, int64_t qi, unsigned char* smem, c
   const int width = a.width;
   const int64_t max_steps = a.n + 16;
   for (int64_t step = 0;; ++step) {
-    const int bn = s.bn, first = s.first;
+    // Block-shared state is read into registers here, before the step's first
+    // barrier; thread 0 rewrites s.bn / s.hcount only after the step's last
+    // merge barrier, so no thread can observe the next step's values early.
+    const int bn = s.bn, first = s.first, hcount = s.hcount;
     if (first >= bn) break;
     if (step >= max_steps) {
       set_error(a.err, UHNSW_ECAPACITY);
@@ -549,7 +562,7 @@ __device__ void run_query(const QueryArgs& a, int64_t qi, unsigned char* smem, c
         const int need = width - npar;
         const int r = __popc(ball & lanemask_lt());
         if (un && r < need) {
-          s.par[npar + r] = (int)bi[cb][pos];
+          s.par[chk_idx(npar + r, 8, 7, a.err)] = (int)bi[cb][pos];
           bi[cb][pos] |= kExpanded;
         }
         npar += min(__popc(ball), need);
@@ -565,22 +578,22 @@ __device__ void run_query(const QueryArgs& a, int64_t qi, unsigned char* smem, c
     for (int b0 = 0; b0 < total; b0 += BLOCK) {
       const int j = b0 + tid;
       int32_t v = -1;
-      if (j < total) v = g.ell0[(int64_t)s.par[j / deg0] * deg0 + (j % deg0)];
+      if (j < total) v = g.ell0[chk_idx(s.par[j / deg0], a.n, 5, a.err) * deg0 + (j % deg0)];
       const bool fresh = v >= 0 && hash_insert(tab, hb, v, a.err);
-      compact_append(fresh, (uint32_t)v, ci, &s.m);
+      compact_append(fresh, (uint32_t)v, ci, &s.m, a.cmax, a.err);
     }
     __syncthreads();
     const int m = s.m;
     nexp += npar;
     nadj += npar;
     nb += m;
-    dist_batch_metric<T, TEAM, CPL, BLOCK>(metric, trav, a.d_pad, qv, ci, cd, m);
+    dist_batch_metric<T, TEAM, CPL, BLOCK>(metric, trav, a.d_pad, qv, ci, cd, m, a.n, a.err);
     if (tid == 0) s.first = INT_MAX;
     __syncthreads();
     const int nbn = block_merge(bd[cb], bi[cb], bn, cd, ci, m, sd, si, bd[cb ^ 1], bi[cb ^ 1], efp,
                                 &s.first);
     cb ^= 1;
-    int hc = s.hcount + m;
+    int hc = hcount + m;
     if (hc > (H >> 1)) {
       for (int j = tid; j < H; j += BLOCK) tab[j] = kEmpty;
       __syncthreads();
@@ -635,6 +648,10 @@ __global__ void __launch_bounds__(BLOCK) uhnsw_search_kernel(const QueryArgs a) 
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ BlockScalars s;
   const SmemLayout L(a.d_pad, a.ef_cap, a.hash_bits, a.cmax, a.k_max, a.vcap);
+  if ((uint32_t)L.total > dynamic_smem_bytes()) {
+    if (threadIdx.x == 0) set_error(a.err, UHNSW_ECAPACITY);
+    return;
+  }
   int64_t qi = blockIdx.x;
   for (;;) {
     if (a.queue_head) {
@@ -655,6 +672,10 @@ __global__ void __launch_bounds__(BLOCK) uhnsw_verify_kernel(const QueryArgs a) 
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ BlockScalars s;
   const SmemLayout L(a.d_pad, 0, 0, a.cmax, a.k_max, a.vcap);
+  if ((uint32_t)L.total > dynamic_smem_bytes()) {
+    if (threadIdx.x == 0) set_error(a.err, UHNSW_ECAPACITY);
+    return;
+  }
   const int64_t qi = blockIdx.x;
   if (qi >= a.nq) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;

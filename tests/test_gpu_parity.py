@@ -282,3 +282,31 @@ def test_tiny_graph_fewer_points_than_k(U):
     assert ids.cpu().numpy().tolist() == [[1, 0, 2, -1, -1]]
     assert np.isinf(dist.cpu().numpy()[0, 3:]).all()
     idx.close()
+
+
+@pytest.mark.parametrize("dtype,persistent", [("f32", False), ("f16", True)])
+def test_large_batch_replicas_agree(U, search_case, dtype, persistent):
+    """Thousands of resident blocks (many per SM) with a small beam, so the
+    visited table resets every few steps: each replicated query must return
+    exactly the result it returns alone, and the device error word stays 0."""
+    cname, w, base, qs, p, g1, g2 = search_case
+    reps = 160
+    qbig = np.tile(qs, (reps, 1))
+    pbig = np.tile(p, reps)
+    idx = U.Index(base, g1, g2, traverse_dtype=dtype)
+    for ef in (16, 48):
+        ids, dist, st = idx.search(dev(qbig), dev(pbig), k=10, ef=ef, persistent=persistent,
+                                   stats=True)
+        one, one_d, _ = idx.search(dev(qs), dev(p), k=10, ef=ef)
+        torch.cuda.synchronize()
+        assert idx.device_status() == 0
+        ids = ids.cpu().numpy().reshape(reps, len(qs), 10)
+        dist = dist.cpu().numpy().reshape(reps, len(qs), 10)
+        one, one_d = one.cpu().numpy(), one_d.cpu().numpy()
+        assert (st.cpu().numpy()[:, 5] == 0).all()
+        for r in range(reps):
+            np.testing.assert_array_equal(ids[r], one)
+            np.testing.assert_array_equal(dist[r], one_d)
+        if ef == 16:
+            assert st.cpu().numpy()[:, 4].max() > 0      # the visited table did reset
+    idx.close()
