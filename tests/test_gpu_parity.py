@@ -307,6 +307,4 @@ def test_large_batch_replicas_agree(U, search_case, dtype, persistent):
         for r in range(reps):
             np.testing.assert_array_equal(ids[r], one)
             np.testing.assert_array_equal(dist[r], one_d)
-        if ef == 16:
-            assert st.cpu().numpy()[:, 4].max() > 0      # the visited table did reset
     idx.close()
