@@ -222,9 +222,10 @@ def run_ours(args, log):
     idx16 = U.Index(base, g1, g2, traverse_dtype="f16")
     gt = ground_truth(w, idx16, q_dev, p_dev, k, log)
 
+    qt = dict(query_threads=args.query_threads)
     forms = {
-        "plain_fp32": dict(index=idx32, opts=dict()),
-        "fp16_batched": dict(index=idx16, opts=dict(persistent=True, use_graph=True)),
+        "plain_fp32": dict(index=idx32, opts=dict(**qt)),
+        "fp16_batched": dict(index=idx16, opts=dict(persistent=True, use_graph=True, **qt)),
     }
     forms = {k_: v for k_, v in forms.items() if k_ in args.forms.split(",")}
     # calibration (untimed): smallest ef meeting the recall target in every p bin
@@ -275,7 +276,7 @@ def run_ours(args, log):
     value = aggregate_value(args.steps * w.nq, world, total_s_max)
 
     # algorithmic bytes of one launch (counted by the kernel's own counters)
-    _, _, st = head["index"].search(q_dev, p_dev, k=k, ef=head["ef"], stats=True)
+    _, _, st = head["index"].search(q_dev, p_dev, k=k, ef=head["ef"], stats=True, **qt)
     st = st.cpu().numpy().astype(np.int64)
     row16, row32 = w.d * 2, w.d * 4
     deg0 = g1["max_degree0"]
@@ -304,7 +305,7 @@ def run_ours(args, log):
     pin_p = torch.from_numpy(p).pin_memory().numpy()
     pin_ids = torch.empty((w.nq, k), dtype=torch.int64).pin_memory().numpy()
     pin_d = torch.empty((w.nq, k), dtype=torch.float32).pin_memory().numpy()
-    e2e_opts = dict(persistent=True)
+    e2e_opts = dict(persistent=True, **qt)
     for _ in range(args.warmup):
         head["index"].search_host(pin_q, pin_p, k=k, ef=head["ef"], out=(pin_ids, pin_d),
                                   stream=stream, **e2e_opts)
@@ -331,6 +332,7 @@ def run_ours(args, log):
                         f"G1/G2 M={w.M} efConstruction={w.ef_construction}",
             "form": "fp16_batched: FP16 traversal rows, FP32 verification, persistent launch, "
                     "CUDA-graph replay",
+            "kernel": "warp per query" if args.query_threads != 128 else "block per query",
             "ef": head["ef"], "t": "ef", "verify": "exact with partial-sum abandon",
             "recall_at_10": round(head["recall"], 4),
             "recall_at_10_min_p_bin": round(head["recall_min_bin"], 4),
@@ -453,6 +455,8 @@ def main():
     ap.add_argument("--ref-queries-per-step", type=int, default=100)
     ap.add_argument("--forms", default="plain_fp32,fp16_batched",
                     help="comma-separated subset of the forms to run (the JSON line needs fp16_batched)")
+    ap.add_argument("--query-threads", type=int, default=32, choices=(32, 128),
+                    help="32: warp-per-query kernel, 128: block-per-query kernel")
     ap.add_argument("--quiet", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

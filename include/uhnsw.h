@@ -112,7 +112,8 @@ typedef struct {
   int32_t persistent;    /* 1: one persistent launch pulling queries from a device queue */
   int32_t use_graph;     /* 1: capture the launch sequence once per call shape, then replay */
   int32_t ef_max;        /* bound on ef' over the batch when per-query ef is given; 0 => 512 */
-  int32_t block_threads; /* threads per query block (64, 128 or 256); 0 => autotuned */
+  int32_t query_threads; /* threads per query: 32 = one warp per query (4 queries per
+                            block), 128 = one block per query; 0 => 32 */
   int32_t* stats;        /* device [nq][UHNSW_NSTATS] int32, or NULL */
   int32_t reserved[4];
 } uhnsw_search_opts;

@@ -320,7 +320,9 @@ namespace {
 
 struct Prepared {
   QueryArgs a;
-  TeamShape shape;
+  TeamShape shape;    // block-per-query kernel
+  WarpShape wshape;   // warp-per-query kernel
+  bool warp;
   size_t smem;
   int grid;
   bool persistent;
@@ -350,8 +352,9 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
     return fail(UHNSW_EINVAL, "uhnsw_search: verify_mode=%d", opts.verify_mode);
   if (opts.search_width < 0 || opts.search_width > 8)
     return fail(UHNSW_EINVAL, "uhnsw_search: search_width=%d not in [0, 8]", opts.search_width);
-  if (opts.block_threads != 0 && opts.block_threads != kBlock)
-    return fail(UHNSW_EINVAL, "uhnsw_search: block_threads=%d unsupported", opts.block_threads);
+  if (opts.query_threads != 0 && opts.query_threads != 32 && opts.query_threads != kBlock)
+    return fail(UHNSW_EINVAL, "uhnsw_search: query_threads=%d not 0, 32 or %d", opts.query_threads,
+                kBlock);
   if (opts.ef_max < 0 || opts.ef_max > UHNSW_MAX_EF)
     return fail(UHNSW_EINVAL, "uhnsw_search: ef_max=%d", opts.ef_max);
 
@@ -367,13 +370,16 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
       deg0 = std::max(deg0, G.deg0);
       deg = std::max(deg, G.deg);
     }
-  const int cmax = std::max({width * deg0, deg, kBlock / 8});
+  const bool warp = opts.query_threads != kBlock;
+  const int cmax = std::max({width * deg0, deg, warp ? 4 : kBlock / 8});
   int hb = next_pow2_bits(4ll * (ef_cap + width * deg0));
   hb = std::max(hb, 9);
   if (hb > 15) return fail(UHNSW_ECAPACITY, "uhnsw_search: visited table too large");
   const SmemLayout L(idx->d_pad, ef_cap, hb, cmax, k_max, 0);
-  TeamShape sh;
-  if (!pick_shape(idx->tdtype, idx->d_pad / (idx->tdtype == UHNSW_F32 ? 4 : 8), &sh))
+  const int chunks = idx->d_pad / (idx->tdtype == UHNSW_F32 ? 4 : 8);
+  TeamShape sh{0, 0};
+  WarpShape wsh{0, 0, 0};
+  if (warp ? !pick_warp_shape(idx->tdtype, chunks, &wsh) : !pick_shape(idx->tdtype, chunks, &sh))
     return fail(UHNSW_ECAPACITY, "uhnsw_search: no kernel shape for d=%d", idx->d);
 
   QueryArgs& a = P->a;
@@ -408,13 +414,19 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   a.err = idx->err;
   a.queue_head = opts.persistent ? idx->queue_head : nullptr;
   P->shape = sh;
-  P->smem = L.total;
+  P->wshape = wsh;
+  P->warp = warp;
+  P->smem = warp ? (size_t)L.total * kWarpsPerBlock : (size_t)L.total;
+  if (P->smem > 227 * 1024)
+    return fail(UHNSW_ECAPACITY, "uhnsw_search: %zu bytes of shared memory per block", P->smem);
   P->persistent = opts.persistent != 0;
-  P->grid = (int)nq;
+  const int64_t per_block = warp ? kWarpsPerBlock : 1;
+  P->grid = (int)((nq + per_block - 1) / per_block);
   if (P->persistent) {
-    const int occ = search_occupancy(idx->tdtype, sh, kBlock, L.total);
-    if (occ < 1) return fail(UHNSW_ECUDA, "uhnsw_search: kernel does not fit (smem %zu)", L.total);
-    P->grid = (int)std::min<int64_t>(nq, (int64_t)occ * idx->num_sms);
+    const int occ = warp ? wsearch_occupancy(idx->tdtype, wsh, P->smem)
+                         : search_occupancy(idx->tdtype, sh, kBlock, P->smem);
+    if (occ < 1) return fail(UHNSW_ECUDA, "uhnsw_search: kernel does not fit (smem %zu)", P->smem);
+    P->grid = (int)std::min<int64_t>(P->grid, (int64_t)occ * idx->num_sms);
   }
   return UHNSW_OK;
 }
@@ -426,7 +438,8 @@ int enqueue_search(uhnsw_index* idx, const Prepared& P, cudaStream_t st) {
     e = cudaMemsetAsync(idx->queue_head, 0, 4, st);
     if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: queue reset");
   }
-  e = launch_search(idx->tdtype, P.shape, P.a, P.grid, kBlock, P.smem, st);
+  e = P.warp ? launch_wsearch(idx->tdtype, P.wshape, P.a, P.grid, P.smem, st)
+             : launch_search(idx->tdtype, P.shape, P.a, P.grid, kBlock, P.smem, st);
   if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: launch");
   return UHNSW_OK;
 }

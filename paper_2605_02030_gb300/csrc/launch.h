@@ -6,7 +6,7 @@
 
 #include <cstdint>
 
-#include "query_kernels.cuh"
+#include "warp_kernels.cuh"
 
 namespace uhnsw_dev {
 
@@ -18,6 +18,17 @@ struct TeamShape {
 
 // Returns false if no compiled shape covers rows of `chunks` 16-byte chunks.
 bool pick_shape(uhnsw_dtype dt, int chunks, TeamShape* out);
+
+// Warp-per-query kernel: TEAM lanes per row, CPL chunks per lane, U rows per
+// team in flight; 4 warps (queries) per block.
+struct WarpShape {
+  int team, cpl, u;
+};
+constexpr int kWarpsPerBlock = 4;
+bool pick_warp_shape(uhnsw_dtype dt, int chunks, WarpShape* out);
+cudaError_t launch_wsearch(uhnsw_dtype dt, WarpShape sh, const QueryArgs& a, int grid,
+                           size_t smem, cudaStream_t st);
+int wsearch_occupancy(uhnsw_dtype dt, WarpShape sh, size_t smem);
 
 // Launch the fused search kernel: one block per query (grid = nq) or, with
 // a.queue_head set, `grid` persistent blocks.
@@ -45,6 +56,15 @@ cudaError_t launch_search_f16(TeamShape sh, const QueryArgs& a, int grid, int bl
 cudaError_t launch_search_bf16(TeamShape sh, const QueryArgs& a, int grid, int block, size_t smem,
                                cudaStream_t st);
 int occupancy_f32(TeamShape sh, int block, size_t smem);
+cudaError_t launch_wsearch_f32(WarpShape sh, const QueryArgs& a, int grid, size_t smem,
+                               cudaStream_t st);
+cudaError_t launch_wsearch_f16(WarpShape sh, const QueryArgs& a, int grid, size_t smem,
+                               cudaStream_t st);
+cudaError_t launch_wsearch_bf16(WarpShape sh, const QueryArgs& a, int grid, size_t smem,
+                                cudaStream_t st);
+int wocc_f32(WarpShape sh, size_t smem);
+int wocc_f16(WarpShape sh, size_t smem);
+int wocc_bf16(WarpShape sh, size_t smem);
 int occupancy_f16(TeamShape sh, int block, size_t smem);
 int occupancy_bf16(TeamShape sh, int block, size_t smem);
 

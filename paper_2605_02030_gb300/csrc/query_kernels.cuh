@@ -402,10 +402,11 @@ __device__ __forceinline__ void write_verified(const QueryArgs& a, int64_t qi, f
   }
 }
 
-__device__ __forceinline__ void write_stats(const QueryArgs& a, int64_t qi, int nb, int np,
-                                            int terms, int nexp, int nres, int status, int graph,
-                                            int nadj) {
-  if (!a.stats || threadIdx.x != 0) return;
+// Per-query counters; the caller lets exactly one thread of the query call it.
+__device__ __forceinline__ void put_stats(const QueryArgs& a, int64_t qi, int nb, int np,
+                                          int terms, int nexp, int nres, int status, int graph,
+                                          int nadj) {
+  if (!a.stats) return;
   int32_t* st = a.stats + qi * UHNSW_NSTATS;
   st[UHNSW_STAT_NB] = nb;
   st[UHNSW_STAT_NP] = np;
@@ -415,6 +416,12 @@ __device__ __forceinline__ void write_stats(const QueryArgs& a, int64_t qi, int 
   st[UHNSW_STAT_STATUS] = status;
   st[UHNSW_STAT_GRAPH] = graph;
   st[UHNSW_STAT_ADJ] = nadj;
+}
+
+__device__ __forceinline__ void write_stats(const QueryArgs& a, int64_t qi, int nb, int np,
+                                            int terms, int nexp, int nres, int status, int graph,
+                                            int nadj) {
+  if (threadIdx.x == 0) put_stats(a, qi, nb, np, terms, nexp, nres, status, graph, nadj);
 }
 
 __device__ __forceinline__ void write_invalid(const QueryArgs& a, int64_t qi, int BLOCKN) {

@@ -46,6 +46,40 @@ bool pick_shape(uhnsw_dtype dt, int chunks, TeamShape* out) {
   return false;
 }
 
+bool pick_warp_shape(uhnsw_dtype dt, int chunks, WarpShape* out) {
+  // chosen for at most 64 registers per thread (8 warps of 4 queries per SM)
+  static const WarpShape f32[] = {{8, 1, 4},  {16, 2, 2}, {32, 2, 2}, {32, 4, 2},
+                                  {32, 8, 1}, {32, 16, 1}};
+  static const WarpShape f16[] = {{8, 1, 4},  {8, 2, 2},  {16, 2, 2}, {32, 2, 2},
+                                  {32, 4, 2}, {32, 8, 1}};
+  const WarpShape* list = dt == UHNSW_F32 ? f32 : f16;
+  for (int i = 0; i < 6; ++i)
+    if (list[i].team * list[i].cpl >= chunks) {
+      *out = list[i];
+      return true;
+    }
+  return false;
+}
+
+cudaError_t launch_wsearch(uhnsw_dtype dt, WarpShape sh, const QueryArgs& a, int grid, size_t smem,
+                           cudaStream_t st) {
+  switch (dt) {
+    case UHNSW_F32: return launch_wsearch_f32(sh, a, grid, smem, st);
+    case UHNSW_F16: return launch_wsearch_f16(sh, a, grid, smem, st);
+    case UHNSW_BF16: return launch_wsearch_bf16(sh, a, grid, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int wsearch_occupancy(uhnsw_dtype dt, WarpShape sh, size_t smem) {
+  switch (dt) {
+    case UHNSW_F32: return wocc_f32(sh, smem);
+    case UHNSW_F16: return wocc_f16(sh, smem);
+    case UHNSW_BF16: return wocc_bf16(sh, smem);
+  }
+  return 0;
+}
+
 cudaError_t launch_search(uhnsw_dtype dt, TeamShape sh, const QueryArgs& a, int grid, int block,
                           size_t smem, cudaStream_t st) {
   switch (dt) {

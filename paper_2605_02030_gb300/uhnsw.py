@@ -58,7 +58,7 @@ class _SearchOpts(C.Structure):
         ("persistent", C.c_int32),
         ("use_graph", C.c_int32),
         ("ef_max", C.c_int32),
-        ("block_threads", C.c_int32),
+        ("query_threads", C.c_int32),
         ("stats", C.c_void_p),
         ("reserved", C.c_int32 * 4),
     ]
@@ -217,7 +217,7 @@ class Index:
 
     # -- helpers
     def _opts(self, t=0, kappa=0, tau=0.0, cutoff=0.0, mode="exact", width=1, persistent=False,
-              use_graph=False, ef_max=0, stats_t=None, block_threads=0):
+              use_graph=False, ef_max=0, stats_t=None, query_threads=0):
         o = _SearchOpts()
         o.t, o.kappa, o.tau, o.cutoff = int(t), int(kappa), float(tau), float(cutoff)
         o.verify_mode = MODES[mode] if isinstance(mode, str) else int(mode)
@@ -225,14 +225,14 @@ class Index:
         o.persistent = int(bool(persistent))
         o.use_graph = int(bool(use_graph))
         o.ef_max = int(ef_max)
-        o.block_threads = int(block_threads)
+        o.query_threads = int(query_threads)
         o.stats = stats_t.data_ptr() if stats_t is not None else None
         return o
 
     def search(self, q, p, k=10, ef=64, *, k_max: int | None = None, t: int = 0, tau: float = 0.0,
                kappa: int = 0, cutoff: float = 0.0, mode: str = "exact", width: int = 1,
                persistent: bool = False, use_graph: bool = False, ef_max: int = 0,
-               stats: bool = False, out=None, stream=None):
+               query_threads: int = 0, stats: bool = False, out=None, stream=None):
         """Algorithm 1 on device tensors.  q: float32 [nq, d] cuda; p: float32 [nq];
         k / ef: int (same for all) or int32 [nq] tensors.  Returns (ids int64
         [nq, k_max], dist float32 [nq, k_max], stats int32 [nq, 8] or None)."""
@@ -250,7 +250,8 @@ class Index:
         else:
             ids, dist = out
         st = torch.zeros((nq, NSTATS), dtype=torch.int32, device=q.device) if stats else None
-        o = self._opts(t, kappa, tau, cutoff, mode, width, persistent, use_graph, ef_max, st)
+        o = self._opts(t, kappa, tau, cutoff, mode, width, persistent, use_graph, ef_max, st,
+                       query_threads)
         _check(lib.uhnsw_search(self._h, _t_ptr(q), _t_ptr(p), _t_ptr(k_t), _t_ptr(ef_t), nq,
                                 k_max, ef_default, C.byref(o), _t_ptr(ids), _t_ptr(dist),
                                 _stream_ptr(stream)))
@@ -274,7 +275,7 @@ class Index:
         else:
             ids, dist = out
         o = self._opts(**{x: kw[x] for x in ("t", "kappa", "tau", "cutoff", "mode", "width",
-                                             "persistent", "ef_max") if x in kw})
+                                             "persistent", "ef_max", "query_threads") if x in kw})
         _check(lib.uhnsw_search_host(self._h, _np_ptr(q), _np_ptr(p), _np_ptr(k_a), _np_ptr(ef_a),
                                      nq, k_max, ef_default, C.byref(o), _np_ptr(ids),
                                      _np_ptr(dist), _stream_ptr(stream)))

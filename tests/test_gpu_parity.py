@@ -143,6 +143,12 @@ CASES = {
 }
 
 
+@pytest.fixture(params=[32, 128], ids=["warp", "block"])
+def qt(request):
+    """threads per query: 32 = warp-per-query kernel, 128 = block-per-query kernel"""
+    return request.param
+
+
 @pytest.fixture(scope="module", params=list(CASES))
 def search_case(request, U):
     name, n, nq, grid, kw = CASES[request.param]
@@ -153,7 +159,7 @@ def search_case(request, U):
 
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("ef", [16, 50, 128])
-def test_deterministic_beam_equals_oracle_search(U, search_case, dtype, ef):
+def test_deterministic_beam_equals_oracle_search(U, search_case, dtype, ef, qt):
     """p = 1 and p = 2 return the first k beam entries directly: with k = ef
     this is the whole beam, which must equal the oracle's SEARCH-LAYER result
     on the same graph id for id (base distances exact on this data)."""
@@ -164,7 +170,7 @@ def test_deterministic_beam_equals_oracle_search(U, search_case, dtype, ef):
     nq = len(qs)
     for pp, metric, g in ((1.0, 1, g1), (2.0, 2, g2)):
         pv = np.full(nq, pp, np.float32)
-        ids, dist, st = idx.search(dev(qs), dev(pv), k=ef, ef=ef, stats=True)
+        ids, dist, st = idx.search(dev(qs), dev(pv), k=ef, ef=ef, stats=True, query_threads=qt)
         ids, dist, st = ids.cpu().numpy(), dist.cpu().numpy(), st.cpu().numpy()
         for i in range(nq):
             rid, rd, _ = oracle.hnsw_search(g, base, qs[i], metric, ef, ef)
@@ -176,7 +182,7 @@ def test_deterministic_beam_equals_oracle_search(U, search_case, dtype, ef):
 
 
 @pytest.mark.parametrize("mode", ["exact", "paper"])
-def test_uhnsw_query_matches_oracle(U, search_case, mode):
+def test_uhnsw_query_matches_oracle(U, search_case, mode, qt):
     """Algorithm 1 end to end (routing, KnnSearch, verification) against the
     oracle on the same graphs, per-query p (including p = 1, 2 and the
     1.4 cutoff on both sides), k = 10, ef = 48, t = ef."""
@@ -185,7 +191,8 @@ def test_uhnsw_query_matches_oracle(U, search_case, mode):
     pv = p.copy()
     pv[:5] = [1.0, 2.0, 1.4, np.nextafter(np.float32(1.4), np.float32(2)), 0.5]
     idx = U.Index(base, g1, g2)
-    ids, dist, st = idx.search(dev(qs), dev(pv), k=10, ef=48, mode=mode, stats=True)
+    ids, dist, st = idx.search(dev(qs), dev(pv), k=10, ef=48, mode=mode, stats=True,
+                               query_threads=qt)
     ids, dist, st = ids.cpu().numpy(), dist.cpu().numpy(), st.cpu().numpy()
     for i in range(nq):
         rid, rd, rst = oracle.uhnsw_query(g1, g2, base, qs[i], pv[i], 10, 48,
@@ -196,14 +203,15 @@ def test_uhnsw_query_matches_oracle(U, search_case, mode):
     idx.close()
 
 
-def test_search_per_query_k_ef_and_padding(U, search_case):
+def test_search_per_query_k_ef_and_padding(U, search_case, qt):
     cname, w, base, qs, p, g1, g2 = search_case
     nq = len(qs)
     rng = np.random.default_rng(3)
     k = rng.integers(1, 21, nq).astype(np.int32)
     ef = np.maximum(rng.integers(8, 90, nq), 1).astype(np.int32)
     idx = U.Index(base, g1, g2)
-    ids, dist, _ = idx.search(dev(qs), dev(p), k=dev(k), ef=dev(ef), k_max=24, ef_max=128)
+    ids, dist, _ = idx.search(dev(qs), dev(p), k=dev(k), ef=dev(ef), k_max=24, ef_max=128,
+                              query_threads=qt)
     ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
     for i in range(nq):
         rid, rd, _ = oracle.uhnsw_query(g1, g2, base, qs[i], p[i], int(k[i]), int(ef[i]))
@@ -212,37 +220,38 @@ def test_search_per_query_k_ef_and_padding(U, search_case):
     idx.close()
 
 
-def test_search_forms_agree_bitwise(U, search_case):
+def test_search_forms_agree_bitwise(U, search_case, qt):
     """Plain launch, persistent launch, CUDA-graph replay, host-buffer call and
     each query alone vs in the batch: identical results (deterministic mode)."""
     cname, w, base, qs, p, g1, g2 = search_case
     idx = U.Index(base, g1, g2, traverse_dtype="f16")
     q, pp = dev(qs), dev(p)
-    a_ids, a_d, _ = idx.search(q, pp, k=10, ef=40)
-    b_ids, b_d, _ = idx.search(q, pp, k=10, ef=40, persistent=True)
-    c_ids, c_d, _ = idx.search(q, pp, k=10, ef=40, persistent=True, use_graph=True)
+    a_ids, a_d, _ = idx.search(q, pp, k=10, ef=40, query_threads=qt)
+    b_ids, b_d, _ = idx.search(q, pp, k=10, ef=40, persistent=True, query_threads=qt)
+    c_ids, c_d, _ = idx.search(q, pp, k=10, ef=40, persistent=True, use_graph=True,
+                               query_threads=qt)
     c2_ids, c2_d, _ = idx.search(q, pp, k=10, ef=40, persistent=True, use_graph=True,
-                                 out=(c_ids, c_d))
-    h_ids, h_d = idx.search_host(qs, p, k=10, ef=40)
+                                 out=(c_ids, c_d), query_threads=qt)
+    h_ids, h_d = idx.search_host(qs, p, k=10, ef=40, query_threads=qt)
     torch.cuda.synchronize()
     for x, y in ((b_ids, b_d), (c_ids, c_d), (c2_ids, c2_d)):
         assert torch.equal(a_ids, x) and torch.equal(a_d, y)
     np.testing.assert_array_equal(a_ids.cpu().numpy(), h_ids)
     np.testing.assert_array_equal(a_d.cpu().numpy(), h_d)
     for i in (0, 7, len(qs) - 1):
-        s_ids, s_d, _ = idx.search(q[i:i + 1], pp[i:i + 1], k=10, ef=40)
+        s_ids, s_d, _ = idx.search(q[i:i + 1], pp[i:i + 1], k=10, ef=40, query_threads=qt)
         assert torch.equal(s_ids[0], a_ids[i]) and torch.equal(s_d[0], a_d[i])
     idx.close()
 
 
-def test_wide_search_recall_and_validity(U, search_case):
+def test_wide_search_recall_and_validity(U, search_case, qt):
     """Several expansions per step (not HNSW's sequential order): results stay
     valid and recall against the exact answer stays high."""
     cname, w, base, qs, p, g1, g2 = search_case
     idx = U.Index(base, g1, g2)
     gt, _ = oracle.exact_knn(base, qs, p, 10)
     for width in (2, 4):
-        ids, dist, _ = idx.search(dev(qs), dev(p), k=10, ef=64, width=width)
+        ids, dist, _ = idx.search(dev(qs), dev(p), k=10, ef=64, width=width, query_threads=qt)
         ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
         for i in range(len(qs)):
             got = ids[i][ids[i] >= 0]
@@ -254,19 +263,21 @@ def test_wide_search_recall_and_validity(U, search_case):
     idx.close()
 
 
-def test_search_invalid_queries_and_edges(U, search_case):
+def test_search_invalid_queries_and_edges(U, search_case, qt):
     cname, w, base, qs, p, g1, g2 = search_case
     idx = U.Index(base, g1, None)
     pv = np.array([0.8, -1.0, 1.9, np.nan], np.float32)   # 1.9 routes to the missing G2
-    ids, dist, st = idx.search(dev(qs[:4]), dev(pv), k=5, ef=20, stats=True)
+    ids, dist, st = idx.search(dev(qs[:4]), dev(pv), k=5, ef=20, stats=True, query_threads=qt)
     st = st.cpu().numpy()
     assert st[0, 5] == 0 and (st[1:, 5] == -1).all()
     assert (ids.cpu().numpy()[1:] == -1).all()
     # k above ef: the beam grows to k
-    ids, dist, _ = idx.search(dev(qs[:2]), dev(np.array([0.9, 0.9], np.float32)), k=30, ef=8)
+    ids, dist, _ = idx.search(dev(qs[:2]), dev(np.array([0.9, 0.9], np.float32)), k=30, ef=8,
+                              query_threads=qt)
     assert (ids.cpu().numpy() >= 0).all()
     # empty batch
-    idx.search(torch.empty((0, w.d), device="cuda"), torch.empty(0, device="cuda"), k=5, ef=20)
+    idx.search(torch.empty((0, w.d), device="cuda"), torch.empty(0, device="cuda"), k=5, ef=20,
+               query_threads=qt)
     torch.cuda.synchronize()
     assert idx.device_status() == 0
     idx.close()
@@ -285,7 +296,7 @@ def test_tiny_graph_fewer_points_than_k(U):
 
 
 @pytest.mark.parametrize("dtype,persistent", [("f32", False), ("f16", True)])
-def test_large_batch_replicas_agree(U, search_case, dtype, persistent):
+def test_large_batch_replicas_agree(U, search_case, dtype, persistent, qt):
     """Thousands of resident blocks (many per SM) with a small beam, so the
     visited table resets every few steps: each replicated query must return
     exactly the result it returns alone, and the device error word stays 0."""
@@ -296,8 +307,8 @@ def test_large_batch_replicas_agree(U, search_case, dtype, persistent):
     idx = U.Index(base, g1, g2, traverse_dtype=dtype)
     for ef in (16, 48):
         ids, dist, st = idx.search(dev(qbig), dev(pbig), k=10, ef=ef, persistent=persistent,
-                                   stats=True)
-        one, one_d, _ = idx.search(dev(qs), dev(p), k=10, ef=ef)
+                                   stats=True, query_threads=qt)
+        one, one_d, _ = idx.search(dev(qs), dev(p), k=10, ef=ef, query_threads=qt)
         torch.cuda.synchronize()
         assert idx.device_status() == 0
         ids = ids.cpu().numpy().reshape(reps, len(qs), 10)
@@ -307,4 +318,18 @@ def test_large_batch_replicas_agree(U, search_case, dtype, persistent):
         for r in range(reps):
             np.testing.assert_array_equal(ids[r], one)
             np.testing.assert_array_equal(dist[r], one_d)
+    idx.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_warp_and_block_kernels_agree(U, search_case, dtype):
+    """The warp-per-query and block-per-query kernels run the same algorithm:
+    on exact data (integer / grid) they return identical ids and distances."""
+    cname, w, base, qs, p, g1, g2 = search_case
+    idx = U.Index(base, g1, g2, traverse_dtype=dtype)
+    for mode in ("exact", "paper"):
+        a = idx.search(dev(qs), dev(p), k=10, ef=40, mode=mode, query_threads=32)
+        b = idx.search(dev(qs), dev(p), k=10, ef=40, mode=mode, query_threads=128)
+        torch.cuda.synchronize()
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
     idx.close()
