@@ -196,6 +196,35 @@ int uhnsw_exact(uhnsw_index* idx, const float* q, const float* p, int64_t nq, in
                 int64_t* out_ids, float* out_dist, void* stream);
 
 /*
+ * uhnsw_exact for callers that cannot allocate device memory.  Such callers
+ * include a serving loop that runs on a fixed, pre-reserved memory budget; a
+ * process whose device memory is owned by another framework's caching
+ * allocator; and latency-critical code that must not hit the device-wide
+ * synchronisation a cudaMalloc or cudaFree can cause.  The paper has no
+ * counterpart: this is an interface detail of this library.
+ *
+ * Identical arguments, results and errors as uhnsw_exact, except:
+ *   - The per-slice partial lists live in one file-scope device array of
+ *     UHNSW_EXACT_STATIC_BYTES bytes.  Every GPU that loads this library holds
+ *     it until the process exits.  The call allocates nothing: no cudaMalloc,
+ *     no cudaFree, no allocating library routine.
+ *   - Sizes: nq * k * 8 bytes must not exceed UHNSW_EXACT_STATIC_BYTES;
+ *     larger requests fail with UHNSW_ECAPACITY before any work is queued.
+ *     Smaller requests may use fewer slices than uhnsw_exact; the result is
+ *     the same.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and caches it.  Make that first call before any
+ *     stream capture begins.  The device must be the index's device.
+ *   - All calls share the array.  It keeps the last call's contents; every
+ *     slot a call reads is written by that call first, so nothing needs
+ *     clearing.  Calls whose work overlaps on the GPU (several streams, or
+ *     several host threads) race on the array: serialise them.
+ */
+#define UHNSW_EXACT_STATIC_BYTES (32 * 1024 * 1024)
+int uhnsw_exact_static(uhnsw_index* idx, const float* q, const float* p, int64_t nq, int32_t k,
+                       int64_t* out_ids, float* out_dist, void* stream);
+
+/*
  * Index facts: n, d, padded row length, bytes held on the device, and the
  * device pointers of the layer-0 tables (for diagnostics).  Any out pointer
  * may be NULL.

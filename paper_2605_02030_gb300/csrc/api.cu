@@ -626,6 +626,60 @@ extern "C" int uhnsw_exact(uhnsw_index* idx, const float* q, const float* p, int
   return UHNSW_OK;
 }
 
+// Scratch of uhnsw_exact_static: the per-slice partial top-k lists (distances
+// then ids) of one call.  Host code must not take this name's address (it is a
+// host-side stand-in); it uses the device address looked up per device below.
+static __device__ __align__(256) unsigned char g_exact_static_scratch[UHNSW_EXACT_STATIC_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {nullptr};
+}  // namespace
+
+extern "C" int uhnsw_exact_static(uhnsw_index* idx, const float* q, const float* p, int64_t nq,
+                                  int32_t k, int64_t* out_ids, float* out_dist, void* stream) {
+  clear_error();
+  if (!idx) return fail(UHNSW_EINVAL, "uhnsw_exact_static: index is NULL");
+  if (nq < 0 || nq > INT32_MAX / 2) return fail(UHNSW_EINVAL, "uhnsw_exact_static: nq");
+  if (k < 1 || k > 256) return fail(UHNSW_EINVAL, "uhnsw_exact_static: k=%d not in [1, 256]", k);
+  if (nq > 0 && (!q || !p || !out_ids || !out_dist))
+    return fail(UHNSW_EINVAL, "uhnsw_exact_static: NULL pointer");
+  const int64_t per_slice = nq * (int64_t)k * 8;
+  if (per_slice > (int64_t)UHNSW_EXACT_STATIC_BYTES)
+    return fail(UHNSW_ECAPACITY, "uhnsw_exact_static: nq*k*8 = %lld bytes exceeds %d",
+                (long long)per_slice, UHNSW_EXACT_STATIC_BYTES);
+  if (nq == 0) return UHNSW_OK;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "uhnsw_exact_static: cudaGetDevice");
+  if (dev != idx->device)
+    return fail(UHNSW_EINVAL, "uhnsw_exact_static: current device %d is not the index's %d", dev,
+                idx->device);
+  if (dev < 0 || dev >= kMaxDevices)
+    return fail(UHNSW_ECAPACITY, "uhnsw_exact_static: device ordinal %d", dev);
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+      void* addr = nullptr;
+      e = cudaGetSymbolAddress(&addr, g_exact_static_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "uhnsw_exact_static: cudaGetSymbolAddress");
+      g_static_addr[dev] = addr;
+    }
+    base = g_static_addr[dev];
+  }
+  int ns = exact_workspace_slices(idx->n, nq, k, idx->num_sms);
+  const int64_t fit = (int64_t)UHNSW_EXACT_STATIC_BYTES / per_slice;
+  if (ns > fit) ns = (int)fit;
+  float* pd = (float*)base;
+  int32_t* pi = (int32_t*)((char*)base + (size_t)ns * nq * k * 4);
+  e = launch_exact(idx->base32, idx->n, idx->d, idx->d_pad, q, p, nq, k, ns, pd, pi, out_ids,
+                   out_dist, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "uhnsw_exact_static: launch");
+  return UHNSW_OK;
+}
+
 extern "C" int uhnsw_index_info(const uhnsw_index* idx, int64_t* n, int32_t* d, int32_t* d_pad,
                                 int64_t* device_bytes, int32_t* max_degree0) {
   clear_error();

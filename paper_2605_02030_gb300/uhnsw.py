@@ -65,6 +65,7 @@ class _SearchOpts(C.Structure):
 
 
 EXPORTS = ("uhnsw_load", "uhnsw_search", "uhnsw_search_host", "uhnsw_verify", "uhnsw_exact",
+           "uhnsw_exact_static",
            "uhnsw_index_info", "uhnsw_device_status", "uhnsw_free", "uhnsw_last_error",
            "uhnsw_build_graph", "uhnsw_built_graph", "uhnsw_built_free")
 
@@ -95,6 +96,8 @@ def load_library():
     lib.uhnsw_verify.argtypes = [P, P, P, P, I32, I32, I64, P, P, P, P]
     lib.uhnsw_exact.restype = C.c_int
     lib.uhnsw_exact.argtypes = [P, P, P, I64, I32, P, P, P]
+    lib.uhnsw_exact_static.restype = C.c_int
+    lib.uhnsw_exact_static.argtypes = [P, P, P, I64, I32, P, P, P]
     lib.uhnsw_index_info.restype = C.c_int
     lib.uhnsw_index_info.argtypes = [P, P, P, P, P, P]
     lib.uhnsw_device_status.restype = C.c_int
