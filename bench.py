@@ -321,6 +321,27 @@ def run_ours(args, log):
     e2e_val = aggregate_value(len(e2e_t) * w.nq, world, e2e_max)
     e2e_recall, _ = recall_per_bin(pin_ids, gt, p, k)
 
+    # serving form: Poisson arrivals through the continuous-batching server
+    serving = []
+    if not args.no_serving:
+        for rate in (50_000, 200_000):
+            arr = np.cumsum(np.random.default_rng(7).exponential(1e6 / rate, size=w.nq))
+            srv = U.Server(head["index"], max_batch=256, streams=4, k_max=k,
+                           ef_max=max(head["ef"], k), max_delay_us=100, **qt)
+            s_ids, _, lat = srv.replay(qs, p, k, head["ef"], arr)
+            sst = srv.stats()
+            srv.close()
+            span_s = float(np.max(arr + lat)) / 1e6
+            s_rec, _ = recall_per_bin(s_ids, gt, p, k)
+            serving.append({"arrival_qps": rate, "achieved_qps": round(w.nq / span_s, 1),
+                            "p50_ms": round(float(np.percentile(lat, 50)) / 1e3, 4),
+                            "p99_ms": round(float(np.percentile(lat, 99)) / 1e3, 4),
+                            "recall_at_10": round(s_rec, 4),
+                            "mean_batch": round(sst["mean_batch"], 2),
+                            "peak_inflight": int(sst["peak_inflight"]), "requests": w.nq})
+            log(f"serving at {rate} QPS: p50 {serving[-1]['p50_ms']} ms, "
+                f"p99 {serving[-1]['p99_ms']} ms")
+
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -357,6 +378,7 @@ def run_ours(args, log):
                 "api": "uhnsw_search_host (pinned host buffers)"},
         "clocks": clocks,
         "gpu_launches": args.steps,
+        "serving": serving,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, base, qs, p, g1, g2, head["ef"], k, args.cpu_seconds)
@@ -450,6 +472,7 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="base size override (smaller runs)")
     ap.add_argument("--nq", type=int, default=0, help="queries per step override")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-ef", type=int, default=128)
     ap.add_argument("--ref-queries-per-step", type=int, default=100)

@@ -115,7 +115,9 @@ typedef struct {
   int32_t query_threads; /* threads per query: 32 = one warp per query (4 queries per
                             block), 128 = one block per query; 0 => 32 */
   int32_t* stats;        /* device [nq][UHNSW_NSTATS] int32, or NULL */
-  int32_t reserved[4];
+  int32_t stage_bytes;   /* warp kernel: shared memory per query for the FP32 rows being
+                            verified (a multiple of 4 rows); 0 => 4 rows */
+  int32_t reserved[3];
 } uhnsw_search_opts;
 
 /*
@@ -241,6 +243,77 @@ void uhnsw_free(uhnsw_index* idx);
 
 /* Message of the calling thread's last failed call ("" if none). */
 const char* uhnsw_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching over a resident index.  The paper answers one
+ * query at a time (Section 4.1.2 measures per-query time); this server lets
+ * requests that arrive while others are on the GPU join the next batch.
+ * ---------------------------------------------------------------------- */
+
+typedef struct uhnsw_server uhnsw_server;
+
+typedef struct {
+  int32_t max_batch;     /* queries per launch; 0 => 1024 */
+  int32_t streams;       /* batches in flight at once (one stream each); 0 => 4 */
+  int64_t state_budget;  /* bytes of search state (beam, visited table, verification lists
+                            of every admitted, unfinished query) admitted at once;
+                            0 => 2 * max_batch queries at ef_max / k_max */
+  int32_t k_max;         /* largest k accepted; 0 => 100 */
+  int32_t ef_max;        /* largest ef accepted; 0 => 512 */
+  int32_t max_delay_us;  /* a partial batch waits at most this long for more requests
+                            while other batches run; 0 => 200 */
+  int32_t reserved;
+  uhnsw_search_opts search; /* options of every launch (stats, use_graph, ef_max ignored) */
+} uhnsw_server_opts;
+
+typedef struct {
+  int64_t completed;     /* requests finished (latencies recorded) */
+  int64_t batches;       /* launches */
+  double mean_batch;     /* queries per launch */
+  int64_t peak_inflight; /* most queries admitted and unfinished at once */
+  int64_t peak_state;    /* most search-state bytes admitted at once (<= state_budget
+                            unless a single request exceeds it) */
+  double mean_us, p50_us, p99_us, max_us; /* submit -> result on the host */
+  int32_t error;         /* first failure of a launch (0 if none) */
+  int32_t reserved;
+} uhnsw_server_report;
+
+/*
+ * Starts a server on `idx` (which must outlive it) with a dispatcher and a
+ * completion thread; allocates max_batch-query device and pinned host slots
+ * per stream.  Uses the current device.  Errors: EINVAL, EOOM, ECUDA.
+ */
+int uhnsw_server_create(uhnsw_index* idx, const uhnsw_server_opts* opts, uhnsw_server** out);
+
+/* Queues one request (q: host, d floats; copied) and returns its ticket.
+ * Thread-safe.  Errors: EINVAL (p, k or ef outside the server's limits). */
+int uhnsw_server_submit(uhnsw_server* s, const float* q, float p, int32_t k, int32_t ef,
+                        uint64_t* ticket);
+
+/* Non-blocking: *done = 1 and the k results copied out (ticket released) once
+ * finished, else *done = 0. */
+int uhnsw_server_poll(uhnsw_server* s, uint64_t ticket, int64_t* ids, float* dist, int32_t* done);
+
+/* Blocks until the request finishes (or timeout_ms: UHNSW_ETIMEOUT). */
+int uhnsw_server_wait(uhnsw_server* s, uint64_t ticket, int64_t* ids, float* dist,
+                      int32_t timeout_ms);
+
+/*
+ * Request loop: submits nq requests (host arrays q [nq][d], p, k, ef) at the
+ * times arrival_us[i] (microseconds after the call starts, ascending), then
+ * waits for all of them.  Results go to out_ids / out_dist [nq][k_max]
+ * (padded with -1 / +inf past each k), latency_us[i] = submit -> result.
+ * Any output pointer may be NULL.
+ */
+int uhnsw_server_replay(uhnsw_server* s, const float* q, const float* p, const int32_t* k,
+                        const int32_t* ef, int64_t nq, const double* arrival_us,
+                        int64_t* out_ids, float* out_dist, double* latency_us,
+                        int32_t timeout_ms);
+
+int uhnsw_server_stats(uhnsw_server* s, uhnsw_server_report* out);
+
+/* Stops the threads, waits for batches in flight and frees the slots. */
+void uhnsw_server_destroy(uhnsw_server* s);
 
 /* ------------------------------------------------------------------------
  * Index construction (Section 2.2, the HNSW insertion the paper builds G1 and

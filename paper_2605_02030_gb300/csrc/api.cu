@@ -357,6 +357,8 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
                 kBlock);
   if (opts.ef_max < 0 || opts.ef_max > UHNSW_MAX_EF)
     return fail(UHNSW_EINVAL, "uhnsw_search: ef_max=%d", opts.ef_max);
+  if (opts.stage_bytes < 0 || opts.stage_bytes > 64 * 1024)
+    return fail(UHNSW_EINVAL, "uhnsw_search: stage_bytes=%d not in [0, 65536]", opts.stage_bytes);
 
   int ef_cap;
   if (ef) ef_cap = opts.ef_max > 0 ? opts.ef_max : UHNSW_MAX_EF;
@@ -375,7 +377,15 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   int hb = next_pow2_bits(4ll * (ef_cap + width * deg0));
   hb = std::max(hb, 9);
   if (hb > 15) return fail(UHNSW_ECAPACITY, "uhnsw_search: visited table too large");
-  const SmemLayout L(idx->d_pad, ef_cap, hb, cmax, k_max, 0);
+  // warp kernel: rows are staged in batches of sb (traversal) and sv (FP32
+  // verification, a multiple of the 4 teams of a warp)
+  int sb = 0, sv = 0, stage = 0;
+  if (warp) {
+    const int vrow = idx->d_pad * 4;
+    sv = std::max(4, (opts.stage_bytes > 0 ? opts.stage_bytes / vrow : 4) & ~3);
+    stage = sv * vrow;
+  }
+  const SmemLayout L(idx->d_pad, ef_cap, hb, cmax, k_max, 0, stage);
   const int chunks = idx->d_pad / (idx->tdtype == UHNSW_F32 ? 4 : 8);
   TeamShape sh{0, 0};
   WarpShape wsh{0, 0, 0};
@@ -413,6 +423,9 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   a.stats = opts.stats;
   a.err = idx->err;
   a.queue_head = opts.persistent ? idx->queue_head : nullptr;
+  a.stage_bytes = stage;
+  a.sb = sb;
+  a.sv = sv;
   P->shape = sh;
   P->wshape = wsh;
   P->warp = warp;
@@ -678,6 +691,31 @@ extern "C" int uhnsw_exact_static(uhnsw_index* idx, const float* q, const float*
                    out_dist, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "uhnsw_exact_static: launch");
   return UHNSW_OK;
+}
+
+int64_t uhnsw_internal::query_state_bytes(const uhnsw_index* idx, int32_t ef, int32_t k,
+                                          const uhnsw_search_opts* o) {
+  if (!idx || ef < 1 || k < 1) return fail(UHNSW_EINVAL, "query_state_bytes: bad argument");
+  uhnsw_search_opts opts;
+  std::memset(&opts, 0, sizeof(opts));
+  if (o) opts = *o;
+  const bool warp = opts.query_threads != kBlock;
+  const int width = std::max(1, opts.search_width);
+  int deg0 = 0, deg = 0;
+  for (auto& G : idx->g)
+    if (G.present) {
+      deg0 = std::max(deg0, G.deg0);
+      deg = std::max(deg, G.deg);
+    }
+  const int efp = std::max(ef, k);
+  const int cmax = std::max({width * deg0, deg, warp ? 4 : kBlock / 8});
+  const int hb = std::max(9, next_pow2_bits(4ll * (efp + width * deg0)));
+  int stage = 0;
+  if (warp) {
+    const int vrow = idx->d_pad * 4;
+    stage = std::max(4, (opts.stage_bytes > 0 ? opts.stage_bytes / vrow : 4) & ~3) * vrow;
+  }
+  return SmemLayout(idx->d_pad, efp, hb, cmax, k, 0, stage).total;
 }
 
 extern "C" int uhnsw_index_info(const uhnsw_index* idx, int64_t* n, int32_t* d, int32_t* d_pad,

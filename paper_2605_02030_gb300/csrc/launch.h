@@ -19,8 +19,8 @@ struct TeamShape {
 // Returns false if no compiled shape covers rows of `chunks` 16-byte chunks.
 bool pick_shape(uhnsw_dtype dt, int chunks, TeamShape* out);
 
-// Warp-per-query kernel: TEAM lanes per row, CPL chunks per lane, U rows per
-// team in flight; 4 warps (queries) per block.
+// Warp-per-query kernel: TEAM lanes per row, CPL 16-byte chunks per lane,
+// U rows per team loaded per round; 4 warps (queries) per block.
 struct WarpShape {
   int team, cpl, u;
 };

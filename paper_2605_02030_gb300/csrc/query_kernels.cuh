@@ -76,16 +76,20 @@ struct QueryArgs {
   int32_t* err;         // sticky device error word
   const int32_t* cand;  // verification-only launch: [nq][cand_t]
   int32_t cand_t;
+  int32_t stage_bytes;  // warp kernel: per-warp staging buffer for cp.async row copies
+  int32_t sb;           // warp kernel: traversal rows staged per batch
+  int32_t sv;           // warp kernel: FP32 rows staged per verification batch (multiple of 4)
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
 // Dynamic shared-memory carve-up (byte offsets), identical on host and device.
 struct SmemLayout {
-  int qs, bd0, bi0, bd1, bi1, hash, cd, ci, sd, si, td0, ti0, td1, ti1, cv, total;
+  int stage, qs, bd0, bi0, bd1, bi1, hash, cd, ci, sd, si, td0, ti0, td1, ti1, cv, total;
   __host__ __device__ SmemLayout(int d_pad, int ef_cap, int hash_bits, int cmax, int k_max,
-                                 int vcap) {
+                                 int vcap, int stage_bytes = 0) {
     int o = 0;
+    stage = o; o += align16(stage_bytes);
     qs = o; o += align16(d_pad * 4);
     bd0 = o; o += align16(ef_cap * 4);
     bi0 = o; o += align16(ef_cap * 4);

@@ -47,11 +47,11 @@ bool pick_shape(uhnsw_dtype dt, int chunks, TeamShape* out) {
 }
 
 bool pick_warp_shape(uhnsw_dtype dt, int chunks, WarpShape* out) {
-  // chosen for at most 64 registers per thread (8 warps of 4 queries per SM)
-  static const WarpShape f32[] = {{8, 1, 4},  {16, 2, 2}, {32, 2, 2}, {32, 4, 2},
-                                  {32, 8, 1}, {32, 16, 1}};
-  static const WarpShape f16[] = {{8, 1, 4},  {8, 2, 2},  {16, 2, 2}, {32, 2, 2},
-                                  {32, 4, 2}, {32, 8, 1}};
+  // chosen for at most 64 registers per thread
+  static const WarpShape f32[] = {{8, 1, 4},  {16, 2, 2}, {32, 2, 2},
+                                  {32, 4, 2}, {32, 8, 1}, {32, 16, 1}};
+  static const WarpShape f16[] = {{8, 1, 4},  {8, 2, 2},  {16, 2, 2},
+                                  {32, 2, 2}, {32, 4, 2}, {32, 8, 1}};
   const WarpShape* list = dt == UHNSW_F32 ? f32 : f16;
   for (int i = 0; i < 6; ++i)
     if (list[i].team * list[i].cpl >= chunks) {

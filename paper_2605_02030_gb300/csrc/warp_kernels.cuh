@@ -10,6 +10,11 @@
 // (adjacency row, then the candidates' rows) whose latency is hidden by the
 // number of queries in flight, not by the width of one query.
 //
+// Candidate rows of the search are loaded into registers, U rows per team of
+// lanes per round; the FP32 rows of the verification are copied into a
+// per-warp staging area with cp.async, a.sv rows at a time, and summed from
+// shared memory.
+//
 // The search order is HNSW's (one expansion per step when width == 1), the
 // merge keeps the best ef' of W and the new candidates by (distance, id), and
 // the verification uses the same 8-lane teams and 32-dimension groups as the
@@ -68,11 +73,118 @@ __device__ __forceinline__ int warp_merge(const float* ld, const uint32_t* li, i
   return total < cap ? total : cap;
 }
 
-// Base distances of ids[0..m) by one warp: TEAM lanes per row, CPL 16-byte
-// chunks per lane, U rows per team in flight per round.
+__device__ __forceinline__ void cp_async16(uint32_t smem_addr, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr), "l"(gsrc)
+               : "memory");
+}
+
+// Waits for this lane's outstanding cp.async copies; the caller follows with
+// __syncwarp() so that every lane's copies are visible to the warp.
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* g) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(g));
+}
+
+// Two FP32 lanes in one 64-bit register: Blackwell's paired FP32 instructions
+// (sub / add / fma .f32x2, IEEE round-to-nearest per element).
+__device__ __forceinline__ uint64_t f2_pack(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float f2_hsum(uint64_t v) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+  return a + b;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// One lane's share of a base distance: the 16-byte chunks v[0..CPL) of a row
+// against the query slice q2 (pairs of FP32), accumulated as even / odd
+// element pairs.  Metric 1: sum |x - q|; metric 2: sum (x - q)^2.
+template <typename T, int CPL, int METRIC>
+__device__ __forceinline__ float lane_partial(const uint4 (&v)[CPL],
+                                              const uint64_t (&q2)[CPL][Elems16<T>::n / 2]) {
+  constexpr int VEC = Elems16<T>::n;
+  uint64_t acc = 0;  // (+0.0f, +0.0f)
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    float x[VEC];
+    unpack16<T>(v[c], x);
+#pragma unroll
+    for (int e = 0; e < VEC / 2; ++e) {
+      const uint64_t df = f2_sub(f2_pack(x[2 * e], x[2 * e + 1]), q2[c][e]);
+      if (METRIC == 1) acc = f2_add(acc, df & 0x7fffffff7fffffffull);
+      else acc = f2_fma(df, df, acc);
+    }
+  }
+  return f2_hsum(acc);
+}
+
+// Copies rows ids[0..nb) (row_chunks 16-byte chunks each, stride `stride`
+// elements of T) into `stage` (row-major) and waits for them.  When a row is
+// a divisor or a multiple of 32 chunks the lane -> (row, chunk) map needs no
+// division.
+template <typename T>
+__device__ __forceinline__ void warp_stage_rows(const T* __restrict__ rows, int stride,
+                                                int row_chunks, const uint32_t* ids, int nb,
+                                                unsigned char* stage, int64_t n, int32_t* err) {
+  constexpr int VEC = 16 / (int)sizeof(T);
+  const int lane = threadIdx.x & 31;
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(stage);
+  if (row_chunks <= 32 && (32 % row_chunks) == 0) {
+    const int per = 32 / row_chunks;
+    const int sub = lane / row_chunks, ch = lane - sub * row_chunks;
+    for (int r0 = 0; r0 < nb; r0 += per) {
+      const int r = r0 + sub;
+      if (r < nb) {
+        const int64_t id = chk_idx((int64_t)(ids[r] & kIdMask), n, 1, err);
+        cp_async16(sbase + (uint32_t)(r * row_chunks + ch) * 16u, rows + id * stride + ch * VEC);
+      }
+    }
+  } else if ((row_chunks & 31) == 0) {
+    for (int r = 0; r < nb; ++r) {
+      const int64_t id = chk_idx((int64_t)(ids[r] & kIdMask), n, 1, err);
+      for (int c0 = 0; c0 < row_chunks; c0 += 32)
+        cp_async16(sbase + (uint32_t)(r * row_chunks + c0 + lane) * 16u,
+                   rows + id * stride + (c0 + lane) * VEC);
+    }
+  } else {
+    const int tot = nb * row_chunks;
+    for (int c = lane; c < tot; c += 32) {
+      const int r = c / row_chunks, ch = c - r * row_chunks;
+      const int64_t id = chk_idx((int64_t)(ids[r] & kIdMask), n, 1, err);
+      cp_async16(sbase + (uint32_t)c * 16u, rows + id * stride + ch * VEC);
+    }
+  }
+  cp_async_wait_all();
+  __syncwarp();
+}
+
+// Base distances of ids[0..m) by one warp.  TEAM lanes per row, CPL 16-byte
+// chunks per lane, U rows per team loaded into registers per round.  (Staging
+// the rows in shared memory with cp.async measured slower here: it cost more
+// in occupancy than it gained in loads in flight.)
 template <typename T, int TEAM, int CPL, int U, int METRIC>
 __device__ __forceinline__ void warp_dist(const T* __restrict__ rows, int d_pad,
-                                          const float (&qv)[CPL][Elems16<T>::n],
+                                          const uint64_t (&q2)[CPL][Elems16<T>::n / 2],
                                           const uint32_t* ids, float* out, int m, int64_t n,
                                           int32_t* err) {
   constexpr int VEC = Elems16<T>::n;
@@ -97,18 +209,7 @@ __device__ __forceinline__ void warp_dist(const T* __restrict__ rows, int d_pad,
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        float x[VEC];
-        unpack16<T>(buf[u][c], x);
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-          const float df = x[e] - qv[c][e];
-          if (METRIC == 1) acc += fabsf(df);
-          else acc = fmaf(df, df, acc);
-        }
-      }
+      float acc = lane_partial<T, CPL, METRIC>(buf[u], q2);
 #pragma unroll
       for (int off = TEAM / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off, TEAM);
       const int i = r * NT * U + u * NT + team;
@@ -120,11 +221,39 @@ __device__ __forceinline__ void warp_dist(const T* __restrict__ rows, int d_pad,
 
 template <typename T, int TEAM, int CPL, int U>
 __device__ __forceinline__ void warp_dist_metric(int metric, const T* rows, int d_pad,
-                                                 const float (&qv)[CPL][Elems16<T>::n],
+                                                 const uint64_t (&q2)[CPL][Elems16<T>::n / 2],
                                                  const uint32_t* ids, float* out, int m,
                                                  int64_t n, int32_t* err) {
-  if (metric == 1) warp_dist<T, TEAM, CPL, U, 1>(rows, d_pad, qv, ids, out, m, n, err);
-  else warp_dist<T, TEAM, CPL, U, 2>(rows, d_pad, qv, ids, out, m, n, err);
+  if (metric == 1) warp_dist<T, TEAM, CPL, U, 1>(rows, d_pad, q2, ids, out, m, n, err);
+  else warp_dist<T, TEAM, CPL, U, 2>(rows, d_pad, q2, ids, out, m, n, err);
+}
+
+// Drops the candidates that cannot enter a full W (those not before its last
+// entry), compacting (cd, ci)[0..m) in place; returns the number kept.
+__device__ __forceinline__ int warp_reject(float* cd, uint32_t* ci, int m, float wd, int32_t wi) {
+  const int lane = threadIdx.x & 31;
+  int cnt = 0;
+  for (int b0 = 0; b0 < m; b0 += 32) {
+    const int i = b0 + lane;
+    float x = 0.f;
+    uint32_t xi = 0;
+    bool keep = false;
+    if (i < m) {
+      x = cd[i];
+      xi = ci[i];
+      keep = pair_lt(x, (int32_t)(xi & kIdMask), wd, wi);
+    }
+    const unsigned ball = __ballot_sync(kFull, keep);
+    __syncwarp();
+    if (keep) {
+      const int pos = cnt + __popc(ball & lanemask_lt());
+      cd[pos] = x;
+      ci[pos] = xi;
+    }
+    cnt += __popc(ball);
+    __syncwarp();
+  }
+  return cnt;
 }
 
 // Appends lanes with keep set to out[*cnt ...] in lane order; *cnt is a
@@ -155,68 +284,105 @@ struct WarpVerify {
   __device__ __forceinline__ uint32_t* ni_() const { return cur ? ti[0] : ti[1]; }
 };
 
-// One wave: 4 candidates C[w0 .. wend) per warp (8 lanes each); finished sums
-// are folded into the running top-k list.
+// L_p sum of a staged FP32 row (shared memory) by a team of 8 lanes, with the
+// same grouping and drop test as lp_sum_team.
 template <int PM>
-__device__ __forceinline__ void warp_verify_wave(const QueryArgs& a, const float* qs, float p,
-                                                 const uint32_t* C, int w0, int wend, int k,
-                                                 WarpVerify& v) {
+__device__ __forceinline__ bool lp_sum_team_staged(const float* srow, int d, int d_pad,
+                                                   const float* qs, float p, float thr,
+                                                   unsigned tmask, int lane8, float& S,
+                                                   int& groups) {
+  float acc = 0.0f;
+  const int G = (d + 31) >> 5;
+  groups = 0;
+  for (int g = 0; g < G; ++g) {
+    const int j = g * 32 + lane8 * 4;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f), qq = x;
+    if (j < d_pad) {
+      x = *reinterpret_cast<const float4*>(srow + j);
+      qq = *reinterpret_cast<const float4*>(qs + j);
+    }
+    acc += pow_term<PM>(fabsf(x.x - qq.x), p);
+    acc += pow_term<PM>(fabsf(x.y - qq.y), p);
+    acc += pow_term<PM>(fabsf(x.z - qq.z), p);
+    acc += pow_term<PM>(fabsf(x.w - qq.w), p);
+    float tot = acc;
+    tot += __shfl_xor_sync(tmask, tot, 1);
+    tot += __shfl_xor_sync(tmask, tot, 2);
+    tot += __shfl_xor_sync(tmask, tot, 4);
+    groups = g + 1;
+    if (tot > thr) return false;
+    S = tot;
+  }
+  return true;
+}
+
+// Verifies C[i0 .. i1): rows are staged a.sv at a time; each wave takes 4
+// staged candidates (8 lanes each) against the running threshold and folds
+// the finished ones into the top-k list.  With fixed_thr set, nothing is
+// dropped (the first K of Algorithm 1).
+template <int PM>
+__device__ __forceinline__ void warp_verify_range(const QueryArgs& a, const float* qs, float p,
+                                                  const uint32_t* C, int i0, int i1, int k,
+                                                  bool no_drop, unsigned char* stage,
+                                                  WarpVerify& v) {
   const int lane = threadIdx.x & 31;
   const int team = lane >> 3, lane8 = lane & 7;
   const unsigned tmask = 0xffu << (team * 8);
-  const int i = w0 + team;
-  bool done = false;
-  float S = 0.f;
-  int groups = 0;
-  int32_t id = 0;
-  if (i < wend) {
-    id = (int32_t)chk_idx((int64_t)(C[i] & kIdMask), a.n, 2, a.err);
-    done = lp_sum_team<PM>(a.base32, a.d, a.d_pad, qs, p, id, v.thr, tmask, lane8, S, groups);
-  }
-  const unsigned leaders = __ballot_sync(kFull, lane8 == 0 && i < wend);
-  const unsigned fin = __ballot_sync(kFull, lane8 == 0 && done);
-  // counters (lane-uniform): candidates started and terms accumulated
-  v.np += __popc(leaders);
-  int tg = (lane8 == 0 && i < wend) ? min(groups * 32, a.d) : 0;
+  const int vchunks = a.d_pad / 4;
+  const float kInf = __int_as_float(0x7f800000);
+  for (int s0 = i0; s0 < i1; s0 += a.sv) {
+    const int nb = min(a.sv, i1 - s0);
+    warp_stage_rows<float>(a.base32, a.d_pad, vchunks, C + s0, nb, stage, a.n, a.err);
+    for (int w0 = 0; w0 < nb; w0 += 4) {
+      const int r = w0 + team;
+      bool done = false;
+      float S = 0.f;
+      int groups = 0;
+      if (r < nb) {
+        const float* srow = reinterpret_cast<const float*>(stage) + (size_t)r * a.d_pad;
+        done = lp_sum_team_staged<PM>(srow, a.d, a.d_pad, qs, p, no_drop ? kInf : v.thr, tmask,
+                                      lane8, S, groups);
+      }
+      const unsigned leaders = __ballot_sync(kFull, lane8 == 0 && r < nb);
+      const unsigned fin = __ballot_sync(kFull, lane8 == 0 && done);
+      v.np += __popc(leaders);
+      int tg = (lane8 == 0 && r < nb) ? min(groups * 32, a.d) : 0;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) tg += __shfl_xor_sync(kFull, tg, off);
-  v.terms += tg;
-  if (lane8 == 0 && done) {
-    const int pos = __popc(fin & lanemask_lt());
-    v.wd[pos] = S;
-    v.wi[pos] = (uint32_t)id;
+      for (int off = 16; off > 0; off >>= 1) tg += __shfl_xor_sync(kFull, tg, off);
+      v.terms += tg;
+      if (lane8 == 0 && done) {
+        const int pos = __popc(fin & lanemask_lt());
+        v.wd[pos] = S;
+        v.wi[pos] = C[s0 + r] & kIdMask;
+      }
+      __syncwarp();
+      v.tn = warp_merge(v.cd_(), v.ci_(), v.tn, v.wd, v.wi, __popc(fin), v.sd, v.si, v.nd_(),
+                        v.ni_(), k, nullptr);
+      v.cur ^= 1;
+      v.thr = v.tn == k ? v.cd_()[k - 1] : kInf;
+    }
+    __syncwarp();
   }
-  __syncwarp();
-  const int wm = __popc(fin);
-  v.tn = warp_merge(v.cd_(), v.ci_(), v.tn, v.wd, v.wi, wm, v.sd, v.si, v.nd_(), v.ni_(), k,
-                    nullptr);
-  v.cur ^= 1;
-  v.thr = v.tn == k ? v.cd_()[k - 1] : __int_as_float(0x7f800000);
 }
 
 template <int PM>
 __device__ void warp_verify_run(const QueryArgs& a, const float* qs, float p, const uint32_t* C,
-                                int t, int k, int kappa, WarpVerify& v) {
-  const float kInf = __int_as_float(0x7f800000);
+                                int t, int k, int kappa, unsigned char* stage, WarpVerify& v) {
   const int lane = threadIdx.x & 31;
   v.tn = 0;
-  v.thr = kInf;
+  v.thr = __int_as_float(0x7f800000);
   if (a.mode != UHNSW_VERIFY_PAPER) {
-    for (int w0 = 0; w0 < t; w0 += 4) warp_verify_wave<PM>(a, qs, p, C, w0, min(w0 + 4, t), k, v);
+    warp_verify_range<PM>(a, qs, p, C, 0, t, k, false, stage, v);
     return;
   }
   const int n0 = min(k, t);
-  for (int w0 = 0; w0 < n0; w0 += 4) {
-    v.thr = kInf;
-    warp_verify_wave<PM>(a, qs, p, C, w0, min(w0 + 4, n0), k, v);
-  }
-  v.thr = v.tn == k ? v.cd_()[k - 1] : kInf;
+  warp_verify_range<PM>(a, qs, p, C, 0, n0, k, true, stage, v);
   int i = n0;
   while (i < t) {
     const int bend = min(i + kappa, t);
     for (int j = lane; j < v.tn; j += 32) v.ci_()[j] |= kExpanded;  // mark R
     __syncwarp();
-    for (int w0 = i; w0 < bend; w0 += 4) warp_verify_wave<PM>(a, qs, p, C, w0, min(w0 + 4, bend), k, v);
+    warp_verify_range<PM>(a, qs, p, C, i, bend, k, false, stage, v);
     i = bend;
     int ov = 0;
     for (int j = lane; j < v.tn; j += 32) ov += (int)(v.ci_()[j] >> 31);
@@ -230,13 +396,13 @@ __device__ void warp_verify_run(const QueryArgs& a, const float* qs, float p, co
 
 __device__ __forceinline__ void warp_verify_dispatch(const QueryArgs& a, const float* qs, float p,
                                                      const uint32_t* C, int t, int k, int kappa,
-                                                     WarpVerify& v) {
+                                                     unsigned char* stage, WarpVerify& v) {
   switch (pmode_of(p)) {
-    case kPOne: warp_verify_run<kPOne>(a, qs, p, C, t, k, kappa, v); break;
-    case kPTwo: warp_verify_run<kPTwo>(a, qs, p, C, t, k, kappa, v); break;
-    case kPHalf: warp_verify_run<kPHalf>(a, qs, p, C, t, k, kappa, v); break;
-    case kPThreeHalves: warp_verify_run<kPThreeHalves>(a, qs, p, C, t, k, kappa, v); break;
-    default: warp_verify_run<kPGeneral>(a, qs, p, C, t, k, kappa, v); break;
+    case kPOne: warp_verify_run<kPOne>(a, qs, p, C, t, k, kappa, stage, v); break;
+    case kPTwo: warp_verify_run<kPTwo>(a, qs, p, C, t, k, kappa, stage, v); break;
+    case kPHalf: warp_verify_run<kPHalf>(a, qs, p, C, t, k, kappa, stage, v); break;
+    case kPThreeHalves: warp_verify_run<kPThreeHalves>(a, qs, p, C, t, k, kappa, stage, v); break;
+    default: warp_verify_run<kPGeneral>(a, qs, p, C, t, k, kappa, stage, v); break;
   }
 }
 
@@ -246,6 +412,7 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
   constexpr int VEC = Elems16<T>::n;
   const int lane = threadIdx.x & 31;
   const float kInf = __int_as_float(0x7f800000);
+  unsigned char* stage = ws + L.stage;
   float* qs = reinterpret_cast<float*>(ws + L.qs);
   float* const bd0 = reinterpret_cast<float*>(ws + L.bd0);
   float* const bd1 = reinterpret_cast<float*>(ws + L.bd1);
@@ -281,15 +448,15 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
   }
   for (int j = lane; j < a.d_pad; j += 32) qs[j] = j < a.d ? a.q[qi * a.d + j] : 0.f;
   __syncwarp();
-  float qv[CPL][VEC];
+  uint64_t q2[CPL][VEC / 2];
   {
     const int lt = lane % TEAM;
 #pragma unroll
     for (int c = 0; c < CPL; ++c)
 #pragma unroll
-      for (int e = 0; e < VEC; ++e) {
-        const int idx = (lt + c * TEAM) * VEC + e;
-        qv[c][e] = idx < a.d_pad ? qs[idx] : 0.f;
+      for (int e = 0; e < VEC / 2; ++e) {
+        const int idx = (lt + c * TEAM) * VEC + 2 * e;
+        q2[c][e] = f2_pack(idx < a.d_pad ? qs[idx] : 0.f, idx + 1 < a.d_pad ? qs[idx + 1] : 0.f);
       }
   }
   const T* trav = reinterpret_cast<const T*>(a.trav);
@@ -298,7 +465,7 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
   // greedy descent through the upper levels
   if (lane == 0) ci[0] = (uint32_t)g.entry;
   __syncwarp();
-  warp_dist_metric<T, TEAM, CPL, U>(metric, trav, a.d_pad, qv, ci, cd, 1, a.n, a.err);
+  warp_dist_metric<T, TEAM, CPL, U>(metric, trav, a.d_pad, q2, ci, cd, 1, a.n, a.err);
   int cur = g.entry;
   float cur_d = cd[0];
   __syncwarp();
@@ -319,7 +486,7 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
       __syncwarp();
       nadj += 1;
       nb += m;
-      warp_dist_metric<T, TEAM, CPL, U>(metric, trav, a.d_pad, qv, ci, cd, m, a.n, a.err);
+      warp_dist_metric<T, TEAM, CPL, U>(metric, trav, a.d_pad, q2, ci, cd, m, a.n, a.err);
       float bdd = kInf;
       int32_t bii = INT_MAX;
       for (int i = lane; i < m; i += 32)
@@ -388,6 +555,18 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
       }
       npar += min(__popc(ball), need);
     }
+    // The next step most likely expands the next unexpanded entry of W: pull
+    // its adjacency row toward L2 while this step runs.
+    {
+      int nxt = -1;
+      for (int b0 = first; b0 < bn && nxt < 0; b0 += 32) {
+        const int pos = b0 + lane;
+        const unsigned un = __ballot_sync(kFull, pos < bn && !(bic[pos] & kExpanded));
+        if (un) nxt = __shfl_sync(kFull, (int)bic[min(b0 + __ffs(un) - 1, bn - 1)], 0);
+      }
+      if (nxt >= 0 && lane < (deg0 * 4 + 127) / 128)
+        prefetch_l2(g.ell0 + chk_idx(nxt, a.n, 5, a.err) * deg0 + lane * 32);
+    }
     __syncwarp();
     const int total = npar * deg0;
     int m = 0;
@@ -404,9 +583,12 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
     nexp += npar;
     nadj += npar;
     nb += m;
-    warp_dist_metric<T, TEAM, CPL, U>(metric, trav, a.d_pad, qv, ci, cd, m, a.n, a.err);
+    warp_dist_metric<T, TEAM, CPL, U>(metric, trav, a.d_pad, q2, ci, cd, m, a.n, a.err);
+    // candidates behind a full W's last entry cannot enter it: drop them before sorting
+    const int mk = bn == efp ? warp_reject(cd, ci, m, bdc[bn - 1], (int32_t)(bic[bn - 1] & kIdMask))
+                             : m;
     int nfirst;
-    const int nbn = warp_merge(bdc, bic, bn, cd, ci, m, sd, si, bdn, bin, efp, &nfirst);
+    const int nbn = warp_merge(bdc, bic, bn, cd, ci, mk, sd, si, bdn, bin, efp, &nfirst);
     {
       float* t0 = bdc;
       bdc = bdn;
@@ -454,7 +636,7 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
   v.sd = sd;
   v.si = si;
   const int kappa = a.kappa > 0 ? a.kappa : k;
-  warp_verify_dispatch(a, qs, p, bic, nc, k, kappa, v);
+  warp_verify_dispatch(a, qs, p, bic, nc, k, kappa, stage, v);
   const double inv_p = 1.0 / (double)p;
   for (int j = lane; j < a.k_max; j += 32) {
     if (j < k && j < v.tn) {
@@ -476,7 +658,7 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
 template <typename T, int TEAM, int CPL, int U, int WARPS, int MINB = UHNSW_WARP_MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB) uhnsw_wsearch_kernel(const QueryArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const SmemLayout L(a.d_pad, a.ef_cap, a.hash_bits, a.cmax, a.k_max, 0);
+  const SmemLayout L(a.d_pad, a.ef_cap, a.hash_bits, a.cmax, a.k_max, 0, a.stage_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if ((uint32_t)(L.total * WARPS) > dynamic_smem_bytes()) {
     if (threadIdx.x == 0) set_error(a.err, UHNSW_ECAPACITY);

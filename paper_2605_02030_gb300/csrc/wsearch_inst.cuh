@@ -30,15 +30,15 @@ int wocc_one(size_t smem) {
 // Calls CALL(T, TEAM, CPL, U) for the compiled warp shape.
 #define UHNSW_WSHAPE_SWITCH(T, SH, CALL)                                     \
   do {                                                                       \
-    const int key_ = (SH).team * 10000 + (SH).cpl * 100 + (SH).u;            \
+    const int key_ = (SH).team * 1000 + (SH).cpl * 10 + (SH).u;              \
     switch (key_) {                                                          \
-      case 80104: return CALL(T, 8, 1, 4);                                   \
-      case 80202: return CALL(T, 8, 2, 2);                                   \
-      case 160202: return CALL(T, 16, 2, 2);                                 \
-      case 320202: return CALL(T, 32, 2, 2);                                 \
-      case 320402: return CALL(T, 32, 4, 2);                                 \
-      case 320801: return CALL(T, 32, 8, 1);                                 \
-      case 321601: return CALL(T, 32, 16, 1);                                \
+      case 8014: return CALL(T, 8, 1, 4);                                    \
+      case 8022: return CALL(T, 8, 2, 2);                                    \
+      case 16022: return CALL(T, 16, 2, 2);                                  \
+      case 32022: return CALL(T, 32, 2, 2);                                  \
+      case 32042: return CALL(T, 32, 4, 2);                                  \
+      case 32081: return CALL(T, 32, 8, 1);                                  \
+      case 32161: return CALL(T, 32, 16, 1);                                 \
       default: return FAIL_VALUE;                                            \
     }                                                                        \
   } while (0)

@@ -60,12 +60,15 @@ class _SearchOpts(C.Structure):
         ("ef_max", C.c_int32),
         ("query_threads", C.c_int32),
         ("stats", C.c_void_p),
-        ("reserved", C.c_int32 * 4),
+        ("stage_bytes", C.c_int32),
+        ("reserved", C.c_int32 * 3),
     ]
 
 
 EXPORTS = ("uhnsw_load", "uhnsw_search", "uhnsw_search_host", "uhnsw_verify", "uhnsw_exact",
-           "uhnsw_exact_static",
+           "uhnsw_exact_static", "uhnsw_server_create", "uhnsw_server_submit", "uhnsw_server_poll",
+           "uhnsw_server_wait", "uhnsw_server_replay", "uhnsw_server_stats",
+           "uhnsw_server_destroy",
            "uhnsw_index_info", "uhnsw_device_status", "uhnsw_free", "uhnsw_last_error",
            "uhnsw_build_graph", "uhnsw_built_graph", "uhnsw_built_free")
 
@@ -104,6 +107,20 @@ def load_library():
     lib.uhnsw_device_status.argtypes = [P]
     lib.uhnsw_free.restype = None
     lib.uhnsw_free.argtypes = [P]
+    lib.uhnsw_server_create.restype = C.c_int
+    lib.uhnsw_server_create.argtypes = [P, P, P]
+    lib.uhnsw_server_submit.restype = C.c_int
+    lib.uhnsw_server_submit.argtypes = [P, P, C.c_float, I32, I32, P]
+    lib.uhnsw_server_poll.restype = C.c_int
+    lib.uhnsw_server_poll.argtypes = [P, C.c_uint64, P, P, P]
+    lib.uhnsw_server_wait.restype = C.c_int
+    lib.uhnsw_server_wait.argtypes = [P, C.c_uint64, P, P, I32]
+    lib.uhnsw_server_replay.restype = C.c_int
+    lib.uhnsw_server_replay.argtypes = [P, P, P, P, P, I64, P, P, P, P, I32]
+    lib.uhnsw_server_stats.restype = C.c_int
+    lib.uhnsw_server_stats.argtypes = [P, P]
+    lib.uhnsw_server_destroy.restype = None
+    lib.uhnsw_server_destroy.argtypes = [P]
     lib.uhnsw_build_graph.restype = C.c_int
     lib.uhnsw_build_graph.argtypes = [P, I64, I32, I32, I32, I32, P, I32, P]
     lib.uhnsw_built_graph.restype = C.c_int
@@ -220,7 +237,7 @@ class Index:
 
     # -- helpers
     def _opts(self, t=0, kappa=0, tau=0.0, cutoff=0.0, mode="exact", width=1, persistent=False,
-              use_graph=False, ef_max=0, stats_t=None, query_threads=0):
+              use_graph=False, ef_max=0, stats_t=None, query_threads=0, stage_bytes=0):
         o = _SearchOpts()
         o.t, o.kappa, o.tau, o.cutoff = int(t), int(kappa), float(tau), float(cutoff)
         o.verify_mode = MODES[mode] if isinstance(mode, str) else int(mode)
@@ -229,13 +246,15 @@ class Index:
         o.use_graph = int(bool(use_graph))
         o.ef_max = int(ef_max)
         o.query_threads = int(query_threads)
+        o.stage_bytes = int(stage_bytes)
         o.stats = stats_t.data_ptr() if stats_t is not None else None
         return o
 
     def search(self, q, p, k=10, ef=64, *, k_max: int | None = None, t: int = 0, tau: float = 0.0,
                kappa: int = 0, cutoff: float = 0.0, mode: str = "exact", width: int = 1,
                persistent: bool = False, use_graph: bool = False, ef_max: int = 0,
-               query_threads: int = 0, stats: bool = False, out=None, stream=None):
+               query_threads: int = 0, stage_bytes: int = 0, stats: bool = False, out=None,
+               stream=None):
         """Algorithm 1 on device tensors.  q: float32 [nq, d] cuda; p: float32 [nq];
         k / ef: int (same for all) or int32 [nq] tensors.  Returns (ids int64
         [nq, k_max], dist float32 [nq, k_max], stats int32 [nq, 8] or None)."""
@@ -246,6 +265,9 @@ class Index:
         ef_t = ef if torch.is_tensor(ef) else None
         if k_max is None:
             k_max = int(k_t.max().item()) if k_t is not None and nq else int(k if k_t is None else 1)
+        elif k_t is None and int(k) != k_max:
+            # one k below the output width: pass it per query (k = NULL means k_max)
+            k_t = torch.full((nq,), int(k), dtype=torch.int32, device=q.device)
         ef_default = int(ef) if ef_t is None else max(1, int(ef_max) or MAX_EF)
         if out is None:
             ids = torch.empty((nq, k_max), dtype=torch.int64, device=q.device)
@@ -254,7 +276,7 @@ class Index:
             ids, dist = out
         st = torch.zeros((nq, NSTATS), dtype=torch.int32, device=q.device) if stats else None
         o = self._opts(t, kappa, tau, cutoff, mode, width, persistent, use_graph, ef_max, st,
-                       query_threads)
+                       query_threads, stage_bytes)
         _check(lib.uhnsw_search(self._h, _t_ptr(q), _t_ptr(p), _t_ptr(k_t), _t_ptr(ef_t), nq,
                                 k_max, ef_default, C.byref(o), _t_ptr(ids), _t_ptr(dist),
                                 _stream_ptr(stream)))
@@ -271,6 +293,8 @@ class Index:
         ef_a = np.ascontiguousarray(ef, np.int32) if isinstance(ef, np.ndarray) else None
         if k_max is None:
             k_max = int(k_a.max()) if k_a is not None else int(k)
+        elif k_a is None and int(k) != k_max:
+            k_a = np.full(nq, int(k), np.int32)
         ef_default = int(ef) if ef_a is None else max(1, int(kw.get("ef_max", 0)) or MAX_EF)
         if out is None:
             ids = np.empty((nq, k_max), np.int64)
@@ -278,7 +302,8 @@ class Index:
         else:
             ids, dist = out
         o = self._opts(**{x: kw[x] for x in ("t", "kappa", "tau", "cutoff", "mode", "width",
-                                             "persistent", "ef_max", "query_threads") if x in kw})
+                                             "persistent", "ef_max", "query_threads",
+                                             "stage_bytes") if x in kw})
         _check(lib.uhnsw_search_host(self._h, _np_ptr(q), _np_ptr(p), _np_ptr(k_a), _np_ptr(ef_a),
                                      nq, k_max, ef_default, C.byref(o), _np_ptr(ids),
                                      _np_ptr(dist), _stream_ptr(stream)))
@@ -323,6 +348,101 @@ class Index:
     def close(self):
         if getattr(self, "_h", None):
             load_library().uhnsw_free(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------- serving
+class _ServerOpts(C.Structure):
+    _fields_ = [
+        ("max_batch", C.c_int32),
+        ("streams", C.c_int32),
+        ("state_budget", C.c_int64),
+        ("k_max", C.c_int32),
+        ("ef_max", C.c_int32),
+        ("max_delay_us", C.c_int32),
+        ("reserved", C.c_int32),
+        ("search", _SearchOpts),
+    ]
+
+
+class _ServerStats(C.Structure):
+    _fields_ = [
+        ("completed", C.c_int64),
+        ("batches", C.c_int64),
+        ("mean_batch", C.c_double),
+        ("peak_inflight", C.c_int64),
+        ("peak_state", C.c_int64),
+        ("mean_us", C.c_double),
+        ("p50_us", C.c_double),
+        ("p99_us", C.c_double),
+        ("max_us", C.c_double),
+        ("error", C.c_int32),
+        ("reserved", C.c_int32),
+    ]
+
+
+class Server:
+    """Continuous-batching server over a loaded Index (uhnsw_server_*)."""
+
+    def __init__(self, index: Index, max_batch: int = 1024, streams: int = 4,
+                 state_budget: int = 0, k_max: int = 100, ef_max: int = 512,
+                 max_delay_us: int = 200, **search_opts):
+        lib = load_library()
+        o = _ServerOpts()
+        o.max_batch, o.streams, o.state_budget = max_batch, streams, state_budget
+        o.k_max, o.ef_max, o.max_delay_us = k_max, ef_max, max_delay_us
+        o.search = index._opts(**search_opts)
+        self.k_max = k_max
+        self.index = index
+        h = C.c_void_p(0)
+        _check(lib.uhnsw_server_create(index._h, C.byref(o), C.byref(h)))
+        self._h = h
+
+    def submit(self, q: np.ndarray, p: float, k: int, ef: int) -> int:
+        q = np.ascontiguousarray(q, np.float32)
+        t = C.c_uint64(0)
+        _check(load_library().uhnsw_server_submit(self._h, _np_ptr(q), float(p), int(k), int(ef),
+                                                  C.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, k: int, timeout_ms: int = 60000):
+        ids = np.empty(k, np.int64)
+        dist = np.empty(k, np.float32)
+        _check(load_library().uhnsw_server_wait(self._h, ticket, _np_ptr(ids), _np_ptr(dist),
+                                                timeout_ms))
+        return ids, dist
+
+    def replay(self, q, p, k, ef, arrival_us, timeout_ms: int = 600000):
+        """Submit requests at arrival_us (ascending, microseconds) from a native
+        thread; returns (ids [nq, k_max], dist [nq, k_max], latency_us [nq])."""
+        q = np.ascontiguousarray(q, np.float32)
+        nq = q.shape[0]
+        p = np.ascontiguousarray(np.broadcast_to(np.asarray(p, np.float32), (nq,)))
+        k = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (nq,)))
+        ef = np.ascontiguousarray(np.broadcast_to(np.asarray(ef, np.int32), (nq,)))
+        arr = np.ascontiguousarray(arrival_us, np.float64)
+        ids = np.empty((nq, self.k_max), np.int64)
+        dist = np.empty((nq, self.k_max), np.float32)
+        lat = np.empty(nq, np.float64)
+        _check(load_library().uhnsw_server_replay(self._h, _np_ptr(q), _np_ptr(p), _np_ptr(k),
+                                                  _np_ptr(ef), nq, _np_ptr(arr), _np_ptr(ids),
+                                                  _np_ptr(dist), _np_ptr(lat), timeout_ms))
+        return ids, dist, lat
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(load_library().uhnsw_server_stats(self._h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in _ServerStats._fields_ if f != "reserved"}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().uhnsw_server_destroy(self._h)
             self._h = None
 
     def __del__(self):  # pragma: no cover
