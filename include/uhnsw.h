@@ -113,11 +113,14 @@ typedef struct {
   int32_t use_graph;     /* 1: capture the launch sequence once per call shape, then replay */
   int32_t ef_max;        /* bound on ef' over the batch when per-query ef is given; 0 => 512 */
   int32_t query_threads; /* threads per query: 32 = one warp per query (4 queries per
-                            block), 128 = one block per query; 0 => 32 */
+                            block), 128 = one block per query; 0 => the configuration
+                            uhnsw_autotune chose for this beam / k bucket, else 32 */
   int32_t* stats;        /* device [nq][UHNSW_NSTATS] int32, or NULL */
   int32_t stage_bytes;   /* warp kernel: shared memory per query for the FP32 rows being
                             verified (a multiple of 4 rows); 0 => 4 rows */
-  int32_t reserved[3];
+  int32_t team_lanes;    /* warp kernel: lanes sharing one row (8, 16 or 32); 0 => the
+                            narrowest compiled team that covers the row */
+  int32_t reserved[2];
 } uhnsw_search_opts;
 
 /*
@@ -225,6 +228,32 @@ int uhnsw_exact(uhnsw_index* idx, const float* q, const float* p, int64_t nq, in
 #define UHNSW_EXACT_STATIC_BYTES (32 * 1024 * 1024)
 int uhnsw_exact_static(uhnsw_index* idx, const float* q, const float* p, int64_t nq, int32_t k,
                        int64_t* out_ids, float* out_dist, void* stream);
+
+/*
+ * Autotuner of the launch configuration (the batched form's team size and
+ * staging width).  Times every candidate on the caller's sample batch (device
+ * q [nq][d], p [nq]; k and ef for all) with 1 warm-up and 3 timed launches on
+ * `stream`, and records the fastest for the bucket (traversal dtype, beam
+ * next_pow2(max(ef, k)), k next_pow2(k)) in the index; uhnsw_search with
+ * opts->query_threads == 0 then uses it.  Candidates: the warp-per-query
+ * kernel with each compiled team width that covers a row (8, 16, 32 lanes)
+ * and 4, 8 or 16 staged verification rows; the block-per-query kernel.  The
+ * candidates run the same algorithm in the same order; their distances can
+ * differ only by FP32 summation order.  `base` supplies the other options
+ * (may be NULL); `best` (may be NULL) receives the chosen options and
+ * `best_ms` (may be NULL) its median time.  The paper has no counterpart
+ * (its queries run one at a time on a CPU).  Synchronises `stream`.
+ * Errors: EINVAL, ECUDA.
+ */
+int uhnsw_autotune(uhnsw_index* idx, const float* q, const float* p, int64_t nq, int32_t k,
+                   int32_t ef, const uhnsw_search_opts* base, void* stream,
+                   uhnsw_search_opts* best, float* best_ms);
+
+/* Writes / reads the tuned configurations as text lines
+ * "dtype d ef_bucket k_bucket query_threads team_lanes stage_bytes"; load
+ * keeps only lines matching this index's dtype and d. */
+int uhnsw_autotune_save(const uhnsw_index* idx, const char* path);
+int uhnsw_autotune_load(uhnsw_index* idx, const char* path);
 
 /*
  * Index facts: n, d, padded row length, bytes held on the device, and the

@@ -97,6 +97,9 @@ struct uhnsw_index {
   // exact-search workspace
   void* exact_ws = nullptr;
   size_t exact_ws_bytes = 0;
+  // autotuned launch configurations: key (ef bucket, k bucket) -> options
+  std::vector<std::pair<int64_t, uhnsw_search_opts>> tuned;
+  std::mutex tuned_mu;
 
   ~uhnsw_index() {
     for (auto& e : graphs) cudaGraphExecDestroy(e.exec);
@@ -357,6 +360,8 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
                 kBlock);
   if (opts.ef_max < 0 || opts.ef_max > UHNSW_MAX_EF)
     return fail(UHNSW_EINVAL, "uhnsw_search: ef_max=%d", opts.ef_max);
+  if (opts.team_lanes != 0 && opts.team_lanes != 8 && opts.team_lanes != 16 && opts.team_lanes != 32)
+    return fail(UHNSW_EINVAL, "uhnsw_search: team_lanes=%d not 0, 8, 16 or 32", opts.team_lanes);
   if (opts.stage_bytes < 0 || opts.stage_bytes > 64 * 1024)
     return fail(UHNSW_EINVAL, "uhnsw_search: stage_bytes=%d not in [0, 65536]", opts.stage_bytes);
 
@@ -365,6 +370,18 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   else ef_cap = std::max({ef_default, opts.t, k_max});
   if (ef_cap > UHNSW_MAX_EF)
     return fail(UHNSW_EINVAL, "uhnsw_search: beam %d exceeds %d", ef_cap, UHNSW_MAX_EF);
+  if (opts.query_threads == 0) {
+    // the autotuned configuration of this bucket, if any
+    const int64_t key = ((int64_t)(1 << next_pow2_bits(ef_cap)) << 16) | (1 << next_pow2_bits(k_max));
+    std::lock_guard<std::mutex> lock(idx->tuned_mu);
+    for (const auto& tv : idx->tuned)
+      if (tv.first == key) {
+        opts.query_threads = tv.second.query_threads;
+        opts.team_lanes = tv.second.team_lanes;
+        opts.stage_bytes = tv.second.stage_bytes;
+        break;
+      }
+  }
   const int width = std::max(1, opts.search_width);
   int deg0 = 0, deg = 0;
   for (auto& G : idx->g)
@@ -389,7 +406,7 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   const int chunks = idx->d_pad / (idx->tdtype == UHNSW_F32 ? 4 : 8);
   TeamShape sh{0, 0};
   WarpShape wsh{0, 0, 0};
-  if (warp ? !pick_warp_shape(idx->tdtype, chunks, &wsh) : !pick_shape(idx->tdtype, chunks, &sh))
+  if (warp ? !pick_warp_shape(idx->tdtype, chunks, opts.team_lanes, &wsh) : !pick_shape(idx->tdtype, chunks, &sh))
     return fail(UHNSW_ECAPACITY, "uhnsw_search: no kernel shape for d=%d", idx->d);
 
   QueryArgs& a = P->a;
@@ -716,6 +733,138 @@ int64_t uhnsw_internal::query_state_bytes(const uhnsw_index* idx, int32_t ef, in
     stage = std::max(4, (opts.stage_bytes > 0 ? opts.stage_bytes / vrow : 4) & ~3) * vrow;
   }
   return SmemLayout(idx->d_pad, efp, hb, cmax, k, 0, stage).total;
+}
+
+extern "C" int uhnsw_autotune(uhnsw_index* idx, const float* q, const float* p, int64_t nq,
+                              int32_t k, int32_t ef, const uhnsw_search_opts* base, void* stream,
+                              uhnsw_search_opts* best, float* best_ms) {
+  clear_error();
+  if (!idx || !q || !p || nq < 1 || k < 1 || ef < 1)
+    return fail(UHNSW_EINVAL, "uhnsw_autotune: bad argument");
+  uhnsw_search_opts b;
+  std::memset(&b, 0, sizeof(b));
+  if (base) b = *base;
+  b.stats = nullptr;
+  b.use_graph = 0;
+  const int efp = std::max({ef, k, b.t});
+  if (efp > UHNSW_MAX_EF) return fail(UHNSW_EINVAL, "uhnsw_autotune: beam %d", efp);
+  const int chunks = idx->d_pad / (idx->tdtype == UHNSW_F32 ? 4 : 8);
+  std::vector<uhnsw_search_opts> cands;
+  for (int team : {8, 16, 32}) {
+    WarpShape ws;
+    if (!pick_warp_shape(idx->tdtype, chunks, team, &ws)) continue;
+    for (int rows : {4, 8, 16}) {
+      uhnsw_search_opts c = b;
+      c.query_threads = 32;
+      c.team_lanes = team;
+      c.stage_bytes = rows * idx->d_pad * 4;
+      cands.push_back(c);
+    }
+  }
+  {
+    uhnsw_search_opts c = b;
+    c.query_threads = kBlock;
+    c.team_lanes = 0;
+    c.stage_bytes = 0;
+    cands.push_back(c);
+  }
+  int64_t* ids = nullptr;
+  float* dist = nullptr;
+  cudaError_t e = cudaMalloc(&ids, nq * k * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&dist, nq * k * 4);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    cudaFree(ids);
+    cudaFree(dist);
+    return cuda_fail(e, "uhnsw_autotune: setup");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  float best_t = 1e30f;
+  int best_i = -1;
+  int rc = UHNSW_OK;
+  for (size_t i = 0; i < cands.size() && rc == UHNSW_OK; ++i) {
+    float ts[3];
+    for (int r = 0; r < 4 && rc == UHNSW_OK; ++r) {
+      cudaEventRecord(e0, st);
+      rc = uhnsw_search(idx, q, p, nullptr, nullptr, nq, k, efp, &cands[i], ids, dist, stream);
+      cudaEventRecord(e1, st);
+      e = cudaEventSynchronize(e1);
+      if (rc == UHNSW_OK && e != cudaSuccess) rc = cuda_fail(e, "uhnsw_autotune: run");
+      if (rc == UHNSW_OK && r > 0) cudaEventElapsedTime(&ts[r - 1], e0, e1);
+    }
+    if (rc != UHNSW_OK) break;
+    std::sort(ts, ts + 3);
+    if (ts[1] < best_t) {
+      best_t = ts[1];
+      best_i = (int)i;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(ids);
+  cudaFree(dist);
+  if (rc != UHNSW_OK) return rc;
+  const int64_t key = ((int64_t)(1 << next_pow2_bits(efp)) << 16) | (1 << next_pow2_bits(k));
+  {
+    std::lock_guard<std::mutex> lock(idx->tuned_mu);
+    bool found = false;
+    for (auto& tv : idx->tuned)
+      if (tv.first == key) {
+        tv.second = cands[best_i];
+        found = true;
+      }
+    if (!found) idx->tuned.emplace_back(key, cands[best_i]);
+  }
+  if (best) *best = cands[best_i];
+  if (best_ms) *best_ms = best_t;
+  return UHNSW_OK;
+}
+
+extern "C" int uhnsw_autotune_save(const uhnsw_index* idx, const char* path) {
+  clear_error();
+  if (!idx || !path) return fail(UHNSW_EINVAL, "uhnsw_autotune_save: NULL argument");
+  FILE* f = fopen(path, "w");
+  if (!f) return fail(UHNSW_EINVAL, "uhnsw_autotune_save: cannot open %s", path);
+  std::lock_guard<std::mutex> lock(const_cast<uhnsw_index*>(idx)->tuned_mu);
+  for (const auto& tv : idx->tuned)
+    fprintf(f, "%d %d %lld %lld %d %d %d\n", (int)idx->tdtype, idx->d, (long long)(tv.first >> 16),
+            (long long)(tv.first & 0xffff), tv.second.query_threads, tv.second.team_lanes,
+            tv.second.stage_bytes);
+  fclose(f);
+  return UHNSW_OK;
+}
+
+extern "C" int uhnsw_autotune_load(uhnsw_index* idx, const char* path) {
+  clear_error();
+  if (!idx || !path) return fail(UHNSW_EINVAL, "uhnsw_autotune_load: NULL argument");
+  FILE* f = fopen(path, "r");
+  if (!f) return fail(UHNSW_EINVAL, "uhnsw_autotune_load: cannot open %s", path);
+  int dt, d, qt, team, stage;
+  long long efb, kb;
+  while (fscanf(f, "%d %d %lld %lld %d %d %d", &dt, &d, &efb, &kb, &qt, &team, &stage) == 7) {
+    if (dt != (int)idx->tdtype || d != idx->d) continue;
+    if ((qt != 32 && qt != kBlock) || (team != 0 && team != 8 && team != 16 && team != 32) ||
+        stage < 0 || stage > 64 * 1024 || efb < 1 || kb < 1)
+      continue;
+    uhnsw_search_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.query_threads = qt;
+    o.team_lanes = team;
+    o.stage_bytes = stage;
+    const int64_t key = (efb << 16) | kb;
+    std::lock_guard<std::mutex> lock(idx->tuned_mu);
+    bool found = false;
+    for (auto& tv : idx->tuned)
+      if (tv.first == key) {
+        tv.second = o;
+        found = true;
+      }
+    if (!found) idx->tuned.emplace_back(key, o);
+  }
+  fclose(f);
+  return UHNSW_OK;
 }
 
 extern "C" int uhnsw_index_info(const uhnsw_index* idx, int64_t* n, int32_t* d, int32_t* d_pad,

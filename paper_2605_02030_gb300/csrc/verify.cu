@@ -46,7 +46,7 @@ bool pick_shape(uhnsw_dtype dt, int chunks, TeamShape* out) {
   return false;
 }
 
-bool pick_warp_shape(uhnsw_dtype dt, int chunks, WarpShape* out) {
+bool pick_warp_shape(uhnsw_dtype dt, int chunks, int team_pref, WarpShape* out) {
   // chosen for at most 64 registers per thread
   static const WarpShape f32[] = {{8, 1, 4},  {16, 2, 2}, {32, 2, 2},
                                   {32, 4, 2}, {32, 8, 1}, {32, 16, 1}};
@@ -54,7 +54,7 @@ bool pick_warp_shape(uhnsw_dtype dt, int chunks, WarpShape* out) {
                                   {32, 2, 2}, {32, 4, 2}, {32, 8, 1}};
   const WarpShape* list = dt == UHNSW_F32 ? f32 : f16;
   for (int i = 0; i < 6; ++i)
-    if (list[i].team * list[i].cpl >= chunks) {
+    if (list[i].team * list[i].cpl >= chunks && (team_pref == 0 || list[i].team == team_pref)) {
       *out = list[i];
       return true;
     }

@@ -61,14 +61,15 @@ class _SearchOpts(C.Structure):
         ("query_threads", C.c_int32),
         ("stats", C.c_void_p),
         ("stage_bytes", C.c_int32),
-        ("reserved", C.c_int32 * 3),
+        ("team_lanes", C.c_int32),
+        ("reserved", C.c_int32 * 2),
     ]
 
 
 EXPORTS = ("uhnsw_load", "uhnsw_search", "uhnsw_search_host", "uhnsw_verify", "uhnsw_exact",
            "uhnsw_exact_static", "uhnsw_server_create", "uhnsw_server_submit", "uhnsw_server_poll",
            "uhnsw_server_wait", "uhnsw_server_replay", "uhnsw_server_stats",
-           "uhnsw_server_destroy",
+           "uhnsw_server_destroy", "uhnsw_autotune", "uhnsw_autotune_save", "uhnsw_autotune_load",
            "uhnsw_index_info", "uhnsw_device_status", "uhnsw_free", "uhnsw_last_error",
            "uhnsw_build_graph", "uhnsw_built_graph", "uhnsw_built_free")
 
@@ -107,6 +108,12 @@ def load_library():
     lib.uhnsw_device_status.argtypes = [P]
     lib.uhnsw_free.restype = None
     lib.uhnsw_free.argtypes = [P]
+    lib.uhnsw_autotune.restype = C.c_int
+    lib.uhnsw_autotune.argtypes = [P, P, P, I64, I32, I32, P, P, P, P]
+    lib.uhnsw_autotune_save.restype = C.c_int
+    lib.uhnsw_autotune_save.argtypes = [P, C.c_char_p]
+    lib.uhnsw_autotune_load.restype = C.c_int
+    lib.uhnsw_autotune_load.argtypes = [P, C.c_char_p]
     lib.uhnsw_server_create.restype = C.c_int
     lib.uhnsw_server_create.argtypes = [P, P, P]
     lib.uhnsw_server_submit.restype = C.c_int
@@ -237,7 +244,8 @@ class Index:
 
     # -- helpers
     def _opts(self, t=0, kappa=0, tau=0.0, cutoff=0.0, mode="exact", width=1, persistent=False,
-              use_graph=False, ef_max=0, stats_t=None, query_threads=0, stage_bytes=0):
+              use_graph=False, ef_max=0, stats_t=None, query_threads=0, stage_bytes=0,
+              team_lanes=0):
         o = _SearchOpts()
         o.t, o.kappa, o.tau, o.cutoff = int(t), int(kappa), float(tau), float(cutoff)
         o.verify_mode = MODES[mode] if isinstance(mode, str) else int(mode)
@@ -247,14 +255,15 @@ class Index:
         o.ef_max = int(ef_max)
         o.query_threads = int(query_threads)
         o.stage_bytes = int(stage_bytes)
+        o.team_lanes = int(team_lanes)
         o.stats = stats_t.data_ptr() if stats_t is not None else None
         return o
 
     def search(self, q, p, k=10, ef=64, *, k_max: int | None = None, t: int = 0, tau: float = 0.0,
                kappa: int = 0, cutoff: float = 0.0, mode: str = "exact", width: int = 1,
                persistent: bool = False, use_graph: bool = False, ef_max: int = 0,
-               query_threads: int = 0, stage_bytes: int = 0, stats: bool = False, out=None,
-               stream=None):
+               query_threads: int = 0, stage_bytes: int = 0, team_lanes: int = 0,
+               stats: bool = False, out=None, stream=None):
         """Algorithm 1 on device tensors.  q: float32 [nq, d] cuda; p: float32 [nq];
         k / ef: int (same for all) or int32 [nq] tensors.  Returns (ids int64
         [nq, k_max], dist float32 [nq, k_max], stats int32 [nq, 8] or None)."""
@@ -276,7 +285,7 @@ class Index:
             ids, dist = out
         st = torch.zeros((nq, NSTATS), dtype=torch.int32, device=q.device) if stats else None
         o = self._opts(t, kappa, tau, cutoff, mode, width, persistent, use_graph, ef_max, st,
-                       query_threads, stage_bytes)
+                       query_threads, stage_bytes, team_lanes)
         _check(lib.uhnsw_search(self._h, _t_ptr(q), _t_ptr(p), _t_ptr(k_t), _t_ptr(ef_t), nq,
                                 k_max, ef_default, C.byref(o), _t_ptr(ids), _t_ptr(dist),
                                 _stream_ptr(stream)))
@@ -303,7 +312,7 @@ class Index:
             ids, dist = out
         o = self._opts(**{x: kw[x] for x in ("t", "kappa", "tau", "cutoff", "mode", "width",
                                              "persistent", "ef_max", "query_threads",
-                                             "stage_bytes") if x in kw})
+                                             "stage_bytes", "team_lanes") if x in kw})
         _check(lib.uhnsw_search_host(self._h, _np_ptr(q), _np_ptr(p), _np_ptr(k_a), _np_ptr(ef_a),
                                      nq, k_max, ef_default, C.byref(o), _np_ptr(ids),
                                      _np_ptr(dist), _stream_ptr(stream)))
@@ -333,6 +342,23 @@ class Index:
         _check(lib.uhnsw_exact(self._h, _t_ptr(q), _t_ptr(p), nq, k, _t_ptr(ids), _t_ptr(dist),
                                _stream_ptr(stream)))
         return ids, dist
+
+    def autotune(self, q, p, k: int, ef: int, stream=None, **base_opts):
+        """uhnsw_autotune on a device sample batch: returns (options dict, ms)."""
+        lib = load_library()
+        b = self._opts(**base_opts)
+        best = _SearchOpts()
+        ms = C.c_float(0)
+        _check(lib.uhnsw_autotune(self._h, _t_ptr(q), _t_ptr(p), q.shape[0], int(k), int(ef),
+                                  C.byref(b), _stream_ptr(stream), C.byref(best), C.byref(ms)))
+        return ({"query_threads": best.query_threads, "team_lanes": best.team_lanes,
+                 "stage_bytes": best.stage_bytes}, ms.value)
+
+    def autotune_save(self, path: str):
+        _check(load_library().uhnsw_autotune_save(self._h, path.encode()))
+
+    def autotune_load(self, path: str):
+        _check(load_library().uhnsw_autotune_load(self._h, path.encode()))
 
     def info(self) -> dict:
         lib = load_library()

@@ -1,0 +1,62 @@
+"""Parity at the bench's full size: 1,000,000 x 128 SIFT-shaped rows, 10,000
+queries, the FP16 batched form (persistent launch, CUDA-graph replay, warp
+per query) at the operating point ef = 48.  The oracle computes sampled
+outputs one by one on the same graphs: its Algorithm 1 result (the FP16
+copy of integer data is exact, so the beam is the oracle's and only L_p
+near-ties may differ) and its exact top-10 for the recall spot check."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_02030_gb300 import inputs as I
+
+from helpers import check_topk
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def full():
+    import paper_2605_02030_gb300 as pkg
+    pkg.build()
+    from paper_2605_02030_gb300 import uhnsw as U
+    import bench
+
+    w = I.WORKLOADS["sift1m"]
+    base = I.base_vectors(w)
+    qs = I.query_vectors(w)
+    p, _, _ = I.query_params(w)
+    g1, g2 = bench.graphs_for(w, base, lambda m: None)
+    idx = U.Index(base, g1, g2, traverse_dtype="f16")
+    yield U, w, base, qs, p, g1, g2, idx
+    idx.close()
+
+
+def test_full_size_sampled_parity(full):
+    U, w, base, qs, p, g1, g2, idx = full
+    q, pp = torch.from_numpy(qs).cuda(), torch.from_numpy(p).cuda()
+    ids, dist, st = idx.search(q, pp, k=10, ef=48, persistent=True, use_graph=True, stats=True)
+    ids2, dist2, _ = idx.search(q, pp, k=10, ef=48, persistent=True, use_graph=True)
+    torch.cuda.synchronize()
+    assert idx.device_status() == 0
+    ids, dist, st = ids.cpu().numpy(), dist.cpu().numpy(), st.cpu().numpy()
+    # the graph replay reproduces the first launch bit for bit
+    assert np.array_equal(ids, ids2.cpu().numpy()) and np.array_equal(dist, dist2.cpu().numpy())
+    assert (st[:, 5] == 0).all()
+    holders = (oracle._CSRHolder(g1), oracle._CSRHolder(g2))
+    sample = np.random.default_rng(0).choice(len(qs), size=24, replace=False)
+    sample[:3] = [int(np.argmax(p == 1.0)), int(np.argmax(p == 2.0)), int(np.argmax(p == 0.5))]
+    for i in sample:
+        rid, rd, rst = oracle.uhnsw_query(g1, g2, base, qs[i], float(p[i]), 10, 48,
+                                          _holders=holders)
+        check_topk(base, qs[i], p[i], ids[i], dist[i], rid, 10, f"query {i} p={p[i]}")
+        assert st[i, 6] == (1 if p[i] == 1.0 else 2 if p[i] == 2.0 else
+                            (1 if p[i] <= np.float32(1.4) else 2))
+    # recall against the oracle's exact answer on a few sampled queries
+    few = sample[:4]
+    gt, _ = oracle.exact_knn(base, qs[few], p[few], 10)
+    hits = sum(len(set(ids[i].tolist()) & set(gt[j].tolist())) for j, i in enumerate(few))
+    assert hits / (10 * len(few)) >= 0.9

@@ -333,3 +333,31 @@ def test_warp_and_block_kernels_agree(U, search_case, dtype):
         torch.cuda.synchronize()
         assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
     idx.close()
+
+
+def test_autotune_picks_a_valid_configuration(U, search_case, tmp_path):
+    """The autotuner times the compiled launch configurations, records the
+    fastest for the bucket, and later searches with query_threads == 0 use it:
+    same ids and distances as the explicit configuration (exact data)."""
+    cname, w, base, qs, p, g1, g2 = search_case
+    idx = U.Index(base, g1, g2, traverse_dtype="f16")
+    q, pp = dev(qs), dev(p)
+    best, ms = idx.autotune(q, pp, 10, 40)
+    assert best["query_threads"] in (32, 128) and ms > 0
+    if best["query_threads"] == 32:
+        assert best["team_lanes"] in (8, 16, 32) and best["stage_bytes"] % (4 * w.d) == 0
+    tuned = idx.search(q, pp, k=10, ef=40)
+    explicit = idx.search(q, pp, k=10, ef=40, **best)
+    torch.cuda.synchronize()
+    assert torch.equal(tuned[0], explicit[0]) and torch.equal(tuned[1], explicit[1])
+    path = str(tmp_path / "tuned.txt")
+    idx.autotune_save(path)
+    line = open(path).read().split()
+    assert len(line) == 7 and int(line[1]) == w.d and int(line[4]) == best["query_threads"]
+    idx2 = U.Index(base, g1, g2, traverse_dtype="f16")
+    idx2.autotune_load(path)
+    again = idx2.search(q, pp, k=10, ef=40)
+    torch.cuda.synchronize()
+    assert torch.equal(again[0], tuned[0]) and torch.equal(again[1], tuned[1])
+    idx.close()
+    idx2.close()
