@@ -109,7 +109,10 @@ typedef struct {
   float cutoff;          /* routing: p <= cutoff searches G1; 0 => 1.4 */
   int32_t verify_mode;   /* uhnsw_verify_mode */
   int32_t search_width;  /* beam entries expanded per step; <= 1 => exactly HNSW's order */
-  int32_t persistent;    /* 1: one persistent launch pulling queries from a device queue */
+  int32_t persistent;    /* 1: persistent launch pulling queries from a device queue; with
+                            per-query ef the queue is bucketed by beam (<= 64, 128, 256,
+                            512), one launch per bucket sized for its beam.  Persistent
+                            searches on one index must not overlap on the GPU. */
   int32_t use_graph;     /* 1: capture the launch sequence once per call shape, then replay */
   int32_t ef_max;        /* bound on ef' over the batch when per-query ef is given; 0 => 512 */
   int32_t query_threads; /* threads per query: 32 = one warp per query (4 queries per
@@ -150,7 +153,11 @@ int uhnsw_load(const float* base, int64_t n, int32_t d, const uhnsw_graph* g1,
  *   out_dist   device, nq x k_max float32 (L_p distance S^(1/p))
  *   opts       may be NULL (defaults above)
  * The beam of a query holds ef' = max(ef, t', k) entries, t' = max(t or ef, k)
- * for general p, t' = k for p in {1, 2}; ef' above the launch bound
+ * for general p, t' = k for p in {1, 2}.  For p in {1, 2} the first k beam
+ * entries are returned directly when the beam ran on the FP32 rows or on an
+ * FP16/BF16 copy that holds every value exactly (checked at load); with an
+ * inexact copy the whole beam is re-ranked by its FP32 base distance, so
+ * returned distances are always FP32 ones.  ef' above the launch bound
  * (opts->ef_max, or ef_default) or UHNSW_MAX_EF, an invalid p or k, fails that
  * query alone (status EINVAL in stats, outputs padded).
  * Errors: EINVAL (host-checkable arguments), ECUDA.

@@ -19,6 +19,8 @@ NVCC = os.environ.get("NVCC", "nvcc")
 # any out-of-range index instead of accessing it.
 CHECK = os.environ.get("UHNSW_CHECK", "0") == "1"
 EXTRA = ["-DUHNSW_CHECK"] if CHECK else []
+# extra nvcc flags for tuning builds, e.g. UHNSW_NVCC_EXTRA="-DUHNSW_WARP_MINB=10"
+EXTRA += os.environ.get("UHNSW_NVCC_EXTRA", "").split()
 
 
 def _sources():

@@ -82,6 +82,7 @@ struct uhnsw_index {
   int64_t n = 0;
   int32_t d = 0, d_pad = 0;
   uhnsw_dtype tdtype = UHNSW_F32;
+  bool trav_exact = true;  // the traversal copy reproduces every FP32 value
   float* base32 = nullptr;
   void* trav = nullptr;
   DevGraph g[2];
@@ -97,6 +98,9 @@ struct uhnsw_index {
   // exact-search workspace
   void* exact_ws = nullptr;
   size_t exact_ws_bytes = 0;
+  // bucketed persistent search: 16 counters + 16 bucket slots + the order array
+  int32_t* bucket_ws = nullptr;
+  int64_t bucket_cap = 0;
   // autotuned launch configurations: key (ef bucket, k bucket) -> options
   std::vector<std::pair<int64_t, uhnsw_search_opts>> tuned;
   std::mutex tuned_mu;
@@ -114,6 +118,7 @@ struct uhnsw_index {
     cudaFree(queue_head);
     cudaFree(stage);
     cudaFree(exact_ws);
+    cudaFree(bucket_ws);
     if (capture_stream) cudaStreamDestroy(capture_stream);
   }
 };
@@ -287,8 +292,16 @@ extern "C" int uhnsw_load(const float* base, int64_t n, int32_t d, const uhnsw_g
       if (e != cudaSuccess) { rc = cuda_fail(e, "uhnsw_load: traversal copy"); break; }
       idx->bytes += row32 / 2 * n;
       e = launch_convert(idx->base32, idx->trav, dt, (int64_t)idx->d_pad * n, 0);
-      if (e == cudaSuccess) e = cudaDeviceSynchronize();
+      unsigned long long* bad = nullptr;
+      if (e == cudaSuccess) e = cudaMalloc(&bad, sizeof(unsigned long long));
+      if (e == cudaSuccess) e = cudaMemset(bad, 0, sizeof(unsigned long long));
+      if (e == cudaSuccess)
+        e = launch_inexact_count(idx->base32, idx->trav, dt, (int64_t)idx->d_pad * n, bad, 0);
+      unsigned long long nbad = 1;
+      if (e == cudaSuccess) e = cudaMemcpy(&nbad, bad, sizeof(nbad), cudaMemcpyDeviceToHost);
+      cudaFree(bad);
       if (e != cudaSuccess) { rc = cuda_fail(e, "uhnsw_load: convert"); break; }
+      idx->trav_exact = nbad == 0;
     }
     const uhnsw_graph* gs[2] = {g1, g2};
     for (int i = 0; i < 2 && rc == UHNSW_OK; ++i) {
@@ -321,6 +334,12 @@ extern "C" int uhnsw_load(const float* base, int64_t n, int32_t d, const uhnsw_g
 
 namespace {
 
+struct Launch {
+  QueryArgs a;
+  size_t smem;
+  int grid;
+};
+
 struct Prepared {
   QueryArgs a;
   TeamShape shape;    // block-per-query kernel
@@ -329,6 +348,11 @@ struct Prepared {
   size_t smem;
   int grid;
   bool persistent;
+  // bucketed persistent search (per-query ef): one launch per beam bucket,
+  // largest first, each sized for its own bucket's beam
+  bool bucketed = false;
+  BeamBuckets bb;
+  std::vector<Launch> launches;
 };
 
 // Validates host-side search arguments and fills the launch description.
@@ -439,6 +463,7 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   a.out_dist = out_dist;
   a.stats = opts.stats;
   a.err = idx->err;
+  a.trav_exact = idx->trav_exact ? 1 : 0;
   a.queue_head = opts.persistent ? idx->queue_head : nullptr;
   a.stage_bytes = stage;
   a.sb = sb;
@@ -458,6 +483,48 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
     if (occ < 1) return fail(UHNSW_ECUDA, "uhnsw_search: kernel does not fit (smem %zu)", P->smem);
     P->grid = (int)std::min<int64_t>(P->grid, (int64_t)occ * idx->num_sms);
   }
+  P->launches.clear();
+  P->bucketed = P->persistent && ef != nullptr && nq > 0;
+  if (P->bucketed) {
+    // beam buckets <= 64, 128, 256, 512, capped at ef_cap
+    P->bb.n = 0;
+    for (int bound : {64, 128, 256, 512})
+      if (bound < ef_cap) P->bb.bound[P->bb.n++] = bound;
+    P->bb.bound[P->bb.n++] = ef_cap;
+    const int64_t need = 32 + nq;
+    if (need > idx->bucket_cap) {
+      cudaFree(idx->bucket_ws);
+      idx->bucket_ws = nullptr;
+      idx->bucket_cap = 0;
+      cudaError_t e = cudaMalloc(&idx->bucket_ws, need * sizeof(int32_t));
+      if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: bucket scratch");
+      idx->bucket_cap = need;
+    }
+    for (int b = P->bb.n - 1; b >= 0; --b) {
+      Launch Lb;
+      Lb.a = a;
+      const int bound = P->bb.bound[b];
+      Lb.a.ef_cap = bound;
+      int bhb = std::max(9, next_pow2_bits(4ll * (bound + width * deg0)));
+      Lb.a.hash_bits = bhb;
+      const SmemLayout Lw(idx->d_pad, bound, bhb, cmax, k_max, 0, stage);
+      Lb.smem = warp ? (size_t)Lw.total * kWarpsPerBlock : (size_t)Lw.total;
+      const int occ = warp ? wsearch_occupancy(idx->tdtype, wsh, Lb.smem)
+                           : search_occupancy(idx->tdtype, sh, kBlock, Lb.smem);
+      if (occ < 1) return fail(UHNSW_ECUDA, "uhnsw_search: bucket kernel does not fit");
+      Lb.grid = (int)std::min<int64_t>(P->grid, (int64_t)occ * idx->num_sms);
+      Lb.a.queue_head = idx->queue_head + b;
+      Lb.a.qorder = idx->bucket_ws + 32;
+      Lb.a.qbucket = idx->bucket_ws + 16 + 2 * b;
+      P->launches.push_back(Lb);
+    }
+  } else {
+    Launch L1;
+    L1.a = a;
+    L1.smem = P->smem;
+    L1.grid = P->grid;
+    P->launches.push_back(L1);
+  }
   return UHNSW_OK;
 }
 
@@ -465,12 +532,18 @@ int enqueue_search(uhnsw_index* idx, const Prepared& P, cudaStream_t st) {
   if (P.a.nq == 0) return UHNSW_OK;
   cudaError_t e;
   if (P.persistent) {
-    e = cudaMemsetAsync(idx->queue_head, 0, 4, st);
+    e = cudaMemsetAsync(idx->queue_head, 0, 16 * sizeof(int32_t), st);
     if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: queue reset");
   }
-  e = P.warp ? launch_wsearch(idx->tdtype, P.wshape, P.a, P.grid, P.smem, st)
-             : launch_search(idx->tdtype, P.shape, P.a, P.grid, kBlock, P.smem, st);
-  if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: launch");
+  if (P.bucketed) {
+    e = launch_bucketing(P.a, P.bb, idx->bucket_ws, idx->bucket_ws + 32, idx->bucket_ws + 16, st);
+    if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: bucketing");
+  }
+  for (const Launch& L : P.launches) {
+    e = P.warp ? launch_wsearch(idx->tdtype, P.wshape, L.a, L.grid, L.smem, st)
+               : launch_search(idx->tdtype, P.shape, L.a, L.grid, kBlock, L.smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: launch");
+  }
   return UHNSW_OK;
 }
 

@@ -42,8 +42,20 @@ int search_occupancy(uhnsw_dtype dt, TeamShape sh, int block, size_t smem);
 
 cudaError_t launch_verify(const QueryArgs& a, int block, size_t smem, cudaStream_t st);
 
+// Beam buckets of a bucketed persistent search (ascending bounds).
+struct BeamBuckets {
+  int n;
+  int bound[8];
+};
+// Groups the query indices by beam bucket into `order` and writes {first
+// slot, count} per bucket into info[2b], info[2b+1] (ws: 16 int32 scratch).
+cudaError_t launch_bucketing(const QueryArgs& a, const BeamBuckets& bb, int32_t* ws,
+                             int32_t* order, int32_t* info, cudaStream_t st);
+
 cudaError_t launch_convert(const float* src, void* dst, uhnsw_dtype dt, int64_t count,
                            cudaStream_t st);
+cudaError_t launch_inexact_count(const float* src, const void* dst, uhnsw_dtype dt, int64_t count,
+                                 unsigned long long* bad, cudaStream_t st);
 
 int exact_workspace_slices(int64_t n, int64_t nq, int k, int num_sms);
 cudaError_t launch_exact(const float* base, int64_t n, int d, int d_pad, const float* q,

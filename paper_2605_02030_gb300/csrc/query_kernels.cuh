@@ -33,6 +33,7 @@
 #pragma once
 
 #include <climits>
+#include <type_traits>
 
 #include "device_common.cuh"
 
@@ -72,10 +73,13 @@ struct QueryArgs {
   int64_t* out_ids;     // [nq][k_max]
   float* out_dist;      // [nq][k_max]
   int32_t* stats;       // [nq][UHNSW_NSTATS] or null
-  int32_t* queue_head;  // persistent launch: next query index; null => blockIdx.x only
+  int32_t* queue_head;  // persistent launch: next query slot; null => blockIdx.x only
+  const int32_t* qorder;   // bucketed launch: query of each slot, grouped by beam bucket
+  const int32_t* qbucket;  // bucketed launch: {first slot, slot count} of this bucket
   int32_t* err;         // sticky device error word
   const int32_t* cand;  // verification-only launch: [nq][cand_t]
   int32_t cand_t;
+  int32_t trav_exact;   // 1: the traversal copy holds every FP32 value exactly
   int32_t stage_bytes;  // warp kernel: per-warp staging buffer for cp.async row copies
   int32_t sb;           // warp kernel: traversal rows staged per batch
   int32_t sv;           // warp kernel: FP32 rows staged per verification batch (multiple of 4)
@@ -328,7 +332,8 @@ __device__ __forceinline__ void verify_fold(int k, const VerifyBufs& vb, BlockSc
 // left in (vb.td[cur], vb.ti[cur]) with s.tn entries.
 template <int BLOCK, int PM>
 __device__ void verify_run(const QueryArgs& a, const float* qs, float p, const uint32_t* C, int t,
-                           int k, int kappa, const VerifyBufs& vb, BlockScalars& s, int& cur) {
+                           int k, int kappa, bool exact, const VerifyBufs& vb, BlockScalars& s,
+                           int& cur) {
   constexpr int NVT = BLOCK / 8;
   const float kInf = __int_as_float(0x7f800000);
   if (threadIdx.x == 0) {
@@ -339,7 +344,7 @@ __device__ void verify_run(const QueryArgs& a, const float* qs, float p, const u
     s.terms = 0;
   }
   __syncthreads();
-  if (a.mode != UHNSW_VERIFY_PAPER) {
+  if (exact || a.mode != UHNSW_VERIFY_PAPER) {
     for (int w0 = 0; w0 < t; w0 += NVT) {
       verify_wave<BLOCK, PM>(a, qs, p, C, w0, min(w0 + NVT, t), s.thr, vb, s);
       verify_fold<BLOCK>(k, vb, s, cur);
@@ -377,13 +382,16 @@ __device__ void verify_run(const QueryArgs& a, const float* qs, float p, const u
 template <int BLOCK>
 __device__ __forceinline__ void verify_dispatch(const QueryArgs& a, const float* qs, float p,
                                                 const uint32_t* C, int t, int k, int kappa,
-                                                const VerifyBufs& vb, BlockScalars& s, int& cur) {
+                                                bool exact, const VerifyBufs& vb, BlockScalars& s,
+                                                int& cur) {
   switch (pmode_of(p)) {
-    case kPOne: verify_run<BLOCK, kPOne>(a, qs, p, C, t, k, kappa, vb, s, cur); break;
-    case kPTwo: verify_run<BLOCK, kPTwo>(a, qs, p, C, t, k, kappa, vb, s, cur); break;
-    case kPHalf: verify_run<BLOCK, kPHalf>(a, qs, p, C, t, k, kappa, vb, s, cur); break;
-    case kPThreeHalves: verify_run<BLOCK, kPThreeHalves>(a, qs, p, C, t, k, kappa, vb, s, cur); break;
-    default: verify_run<BLOCK, kPGeneral>(a, qs, p, C, t, k, kappa, vb, s, cur); break;
+    case kPOne: verify_run<BLOCK, kPOne>(a, qs, p, C, t, k, kappa, exact, vb, s, cur); break;
+    case kPTwo: verify_run<BLOCK, kPTwo>(a, qs, p, C, t, k, kappa, exact, vb, s, cur); break;
+    case kPHalf: verify_run<BLOCK, kPHalf>(a, qs, p, C, t, k, kappa, exact, vb, s, cur); break;
+    case kPThreeHalves:
+      verify_run<BLOCK, kPThreeHalves>(a, qs, p, C, t, k, kappa, exact, vb, s, cur);
+      break;
+    default: verify_run<BLOCK, kPGeneral>(a, qs, p, C, t, k, kappa, exact, vb, s, cur); break;
   }
 }
 
@@ -621,10 +629,14 @@ __device__ void run_query(const QueryArgs& a, int64_t qi, unsigned char* smem, c
 
   // 4-6. candidate set, verification and output
   const int bn = s.bn;
-  const int nc = min(tt, bn);
+  // p in {1, 2}: the beam's first k directly on FP32 rows (or on an exact
+  // FP16/BF16 copy); on an inexact copy the whole beam is re-ranked by its
+  // FP32 base distance.
+  const bool reduced = !std::is_same<T, float>::value && !a.trav_exact;
+  const int nc = (direct && reduced) ? bn : min(tt, bn);
   int64_t* oid = a.out_ids + qi * a.k_max;
   float* odist = a.out_dist + qi * a.k_max;
-  if (direct) {
+  if (direct && !reduced) {
     for (int j = tid; j < a.k_max; j += BLOCK) {
       if (j < k && j < bn) {
         oid[j] = (int64_t)(bi[cb][j] & kIdMask);
@@ -649,7 +661,7 @@ __device__ void run_query(const QueryArgs& a, int64_t qi, unsigned char* smem, c
   vb.si = si;
   int vc = 0;
   const int kappa = a.kappa > 0 ? a.kappa : k;
-  verify_dispatch<BLOCK>(a, qs, p, bi[cb], nc, k, kappa, vb, s, vc);
+  verify_dispatch<BLOCK>(a, qs, p, bi[cb], nc, k, kappa, direct, vb, s, vc);
   write_verified<BLOCK>(a, qi, p, k, vb, s, vc);
   write_stats(a, qi, nb, s.np, s.terms, nexp, nres, 0, metric, nadj);
 }
@@ -666,7 +678,10 @@ __global__ void __launch_bounds__(BLOCK) uhnsw_search_kernel(const QueryArgs a) 
   int64_t qi = blockIdx.x;
   for (;;) {
     if (a.queue_head) {
-      if (threadIdx.x == 0) s.qi = atomicAdd(a.queue_head, 1);
+      if (threadIdx.x == 0) {
+        const int slot = atomicAdd(a.queue_head, 1);
+        s.qi = !a.qbucket ? slot : (slot < a.qbucket[1] ? a.qorder[a.qbucket[0] + slot] : (int)a.nq);
+      }
       __syncthreads();
       qi = s.qi;
     }
@@ -728,7 +743,7 @@ __global__ void __launch_bounds__(BLOCK) uhnsw_verify_kernel(const QueryArgs a) 
   vb.si = reinterpret_cast<uint32_t*>(smem + L.si);
   int vc = 0;
   const int kappa = a.kappa > 0 ? a.kappa : k;
-  verify_dispatch<BLOCK>(a, qs, p, cv, tv, k, kappa, vb, s, vc);
+  verify_dispatch<BLOCK>(a, qs, p, cv, tv, k, kappa, false, vb, s, vc);
   write_verified<BLOCK>(a, qi, p, k, vb, s, vc);
   write_stats(a, qi, 0, s.np, s.terms, 0, 0, 0, 0, 0);
 }

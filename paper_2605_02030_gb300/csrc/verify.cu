@@ -24,6 +24,28 @@ __global__ void convert_kernel(const float* __restrict__ src, void* dst, int dt,
   }
 }
 
+// Counts the elements whose FP16 / BF16 copy differs from the FP32 value.
+__global__ void inexact_kernel(const float* __restrict__ src, const void* dst, int dt,
+                               int64_t count, unsigned long long* bad) {
+  unsigned long long mine = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float back = dt == UHNSW_F16 ? __half2float(reinterpret_cast<const __half*>(dst)[i])
+                                       : __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(dst)[i]);
+    mine += back != src[i];
+  }
+  if (mine) atomicAdd(bad, mine);
+}
+
+cudaError_t launch_inexact_count(const float* src, const void* dst, uhnsw_dtype dt, int64_t count,
+                                 unsigned long long* bad, cudaStream_t st) {
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks < 1) blocks = 1;
+  inexact_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, dst, (int)dt, count, bad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_convert(const float* src, void* dst, uhnsw_dtype dt, int64_t count,
                            cudaStream_t st) {
   int64_t blocks = (count + 255) / 256;
@@ -44,6 +66,68 @@ bool pick_shape(uhnsw_dtype dt, int chunks, TeamShape* out) {
       return true;
     }
   return false;
+}
+
+// Beam ef' of a query exactly as the search kernels derive it.
+__device__ __forceinline__ int query_beam(float p, int k, int ef, int t) {
+  const bool direct = (p == 1.0f) || (p == 2.0f);
+  int tt = direct ? k : (t > 0 ? t : ef);
+  if (tt < k) tt = k;
+  return max(ef, tt);
+}
+
+__device__ __forceinline__ int beam_bucket(const BeamBuckets& bb, int efp) {
+  for (int b = 0; b < bb.n; ++b)
+    if (efp <= bb.bound[b]) return b;
+  return bb.n - 1;  // beyond every bound: the query fails validation there
+}
+
+// Counting sort of the query indices by beam bucket: counts, then slots.
+// ws[0..8): counts, ws[8..16): cursors, info[2b] = first slot, info[2b+1] = count.
+__global__ void bucket_count_kernel(const float* p, const int32_t* k, const int32_t* ef, int64_t nq,
+                                    int k_max, int ef_default, int t, BeamBuckets bb,
+                                    int32_t* ws) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = beam_bucket(bb, query_beam(p[i], k ? k[i] : k_max, ef ? ef[i] : ef_default, t));
+    atomicAdd(&ws[b], 1);
+  }
+}
+
+__global__ void bucket_scatter_kernel(const float* p, const int32_t* k, const int32_t* ef,
+                                      int64_t nq, int k_max, int ef_default, int t,
+                                      BeamBuckets bb, int32_t* ws, int32_t* order, int32_t* info) {
+  int base[8];
+  int acc = 0;
+  for (int b = 0; b < bb.n; ++b) {
+    base[b] = acc;
+    acc += ws[b];
+  }
+  if (blockIdx.x == 0 && threadIdx.x < bb.n) {
+    info[2 * threadIdx.x] = base[threadIdx.x];
+    info[2 * threadIdx.x + 1] = ws[threadIdx.x];
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = beam_bucket(bb, query_beam(p[i], k ? k[i] : k_max, ef ? ef[i] : ef_default, t));
+    const int pos = atomicAdd(&ws[8 + b], 1);
+    order[base[b] + pos] = (int32_t)i;
+  }
+}
+
+cudaError_t launch_bucketing(const QueryArgs& a, const BeamBuckets& bb, int32_t* ws,
+                             int32_t* order, int32_t* info, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(ws, 0, 16 * sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  int64_t blocks = (a.nq + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  bucket_count_kernel<<<(unsigned)blocks, 256, 0, st>>>(a.p, a.k, a.ef, a.nq, a.k_max,
+                                                         a.ef_default, a.t, bb, ws);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  bucket_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(a.p, a.k, a.ef, a.nq, a.k_max,
+                                                           a.ef_default, a.t, bb, ws, order, info);
+  return cudaGetLastError();
 }
 
 bool pick_warp_shape(uhnsw_dtype dt, int chunks, int team_pref, WarpShape* out) {

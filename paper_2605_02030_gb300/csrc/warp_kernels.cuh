@@ -367,11 +367,12 @@ __device__ __forceinline__ void warp_verify_range(const QueryArgs& a, const floa
 
 template <int PM>
 __device__ void warp_verify_run(const QueryArgs& a, const float* qs, float p, const uint32_t* C,
-                                int t, int k, int kappa, unsigned char* stage, WarpVerify& v) {
+                                int t, int k, int kappa, bool exact, unsigned char* stage,
+                                WarpVerify& v) {
   const int lane = threadIdx.x & 31;
   v.tn = 0;
   v.thr = __int_as_float(0x7f800000);
-  if (a.mode != UHNSW_VERIFY_PAPER) {
+  if (exact || a.mode != UHNSW_VERIFY_PAPER) {
     warp_verify_range<PM>(a, qs, p, C, 0, t, k, false, stage, v);
     return;
   }
@@ -396,13 +397,16 @@ __device__ void warp_verify_run(const QueryArgs& a, const float* qs, float p, co
 
 __device__ __forceinline__ void warp_verify_dispatch(const QueryArgs& a, const float* qs, float p,
                                                      const uint32_t* C, int t, int k, int kappa,
-                                                     unsigned char* stage, WarpVerify& v) {
+                                                     bool exact, unsigned char* stage,
+                                                     WarpVerify& v) {
   switch (pmode_of(p)) {
-    case kPOne: warp_verify_run<kPOne>(a, qs, p, C, t, k, kappa, stage, v); break;
-    case kPTwo: warp_verify_run<kPTwo>(a, qs, p, C, t, k, kappa, stage, v); break;
-    case kPHalf: warp_verify_run<kPHalf>(a, qs, p, C, t, k, kappa, stage, v); break;
-    case kPThreeHalves: warp_verify_run<kPThreeHalves>(a, qs, p, C, t, k, kappa, stage, v); break;
-    default: warp_verify_run<kPGeneral>(a, qs, p, C, t, k, kappa, stage, v); break;
+    case kPOne: warp_verify_run<kPOne>(a, qs, p, C, t, k, kappa, exact, stage, v); break;
+    case kPTwo: warp_verify_run<kPTwo>(a, qs, p, C, t, k, kappa, exact, stage, v); break;
+    case kPHalf: warp_verify_run<kPHalf>(a, qs, p, C, t, k, kappa, exact, stage, v); break;
+    case kPThreeHalves:
+      warp_verify_run<kPThreeHalves>(a, qs, p, C, t, k, kappa, exact, stage, v);
+      break;
+    default: warp_verify_run<kPGeneral>(a, qs, p, C, t, k, kappa, exact, stage, v); break;
   }
 }
 
@@ -611,8 +615,13 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
     hcount = hc;
   }
 
-  const int nc = min(tt, bn);
-  if (direct) {
+  // p in {1, 2} returns the beam's first k directly when the beam ran on the
+  // FP32 rows or on an FP16/BF16 copy that holds every value exactly; on an
+  // inexact copy the whole beam is re-ranked by its FP32 base distance, so
+  // that returned distances are FP32 ones.
+  const bool reduced = !std::is_same<T, float>::value && !a.trav_exact;
+  const int nc = (direct && reduced) ? bn : min(tt, bn);
+  if (direct && !reduced) {
     for (int j = lane; j < a.k_max; j += 32) {
       if (j < k && j < bn) {
         oid[j] = (int64_t)(bic[j] & kIdMask);
@@ -636,7 +645,7 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
   v.sd = sd;
   v.si = si;
   const int kappa = a.kappa > 0 ? a.kappa : k;
-  warp_verify_dispatch(a, qs, p, bic, nc, k, kappa, stage, v);
+  warp_verify_dispatch(a, qs, p, bic, nc, k, kappa, direct, stage, v);
   const double inv_p = 1.0 / (double)p;
   for (int j = lane; j < a.k_max; j += 32) {
     if (j < k && j < v.tn) {
@@ -669,7 +678,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) uhnsw_wsearch_kernel(const Q
   for (;;) {
     if (a.queue_head) {
       int v = 0;
-      if (lane == 0) v = atomicAdd(a.queue_head, 1);
+      if (lane == 0) {
+        const int slot = atomicAdd(a.queue_head, 1);
+        v = !a.qbucket ? slot : (slot < a.qbucket[1] ? a.qorder[a.qbucket[0] + slot] : (int)a.nq);
+      }
       qi = __shfl_sync(kFull, v, 0);
     }
     if (qi >= a.nq) break;

@@ -361,3 +361,26 @@ def test_autotune_picks_a_valid_configuration(U, search_case, tmp_path):
     assert torch.equal(again[0], tuned[0]) and torch.equal(again[1], tuned[1])
     idx.close()
     idx2.close()
+
+
+def test_bucketed_persistent_queue_matches_plain(U, search_case, qt):
+    """Per-query ef across several beam buckets: the bucketed persistent launch
+    (one launch per bucket) returns what one plain launch returns."""
+    cname, w, base, qs, p, g1, g2 = search_case
+    rng = np.random.default_rng(9)
+    nq = len(qs)
+    k = rng.choice([1, 10, 20], size=nq).astype(np.int32)
+    ef = rng.choice([16, 40, 100, 200, 300], size=nq).astype(np.int32)
+    idx = U.Index(base, g1, g2, traverse_dtype="f16")
+    a = idx.search(dev(qs), dev(p), k=dev(k), ef=dev(ef), k_max=20, ef_max=300,
+                   query_threads=qt, stats=True)
+    b = idx.search(dev(qs), dev(p), k=dev(k), ef=dev(ef), k_max=20, ef_max=300,
+                   query_threads=qt, persistent=True, stats=True)
+    c = idx.search(dev(qs), dev(p), k=dev(k), ef=dev(ef), k_max=20, ef_max=300,
+                   query_threads=qt, persistent=True, use_graph=True)
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    assert torch.equal(a[0], c[0]) and torch.equal(a[1], c[1])
+    assert (b[2].cpu().numpy()[:, 5] == 0).all()
+    assert idx.device_status() == 0
+    idx.close()
