@@ -109,10 +109,12 @@ typedef struct {
   float cutoff;          /* routing: p <= cutoff searches G1; 0 => 1.4 */
   int32_t verify_mode;   /* uhnsw_verify_mode */
   int32_t search_width;  /* beam entries expanded per step; <= 1 => exactly HNSW's order */
-  int32_t persistent;    /* 1: persistent launch pulling queries from a device queue; with
-                            per-query ef the queue is bucketed by beam (<= 64, 128, 256,
-                            512), one launch per bucket sized for its beam.  Persistent
-                            searches on one index must not overlap on the GPU. */
+  int32_t persistent;    /* 1: persistent launch pulling queries from a device queue.  The
+                            queue is ordered by graph and p form, so that the queries in
+                            flight on an SM run the same code.  With per-query ef it is
+                            also bucketed by beam (<= 64, 128, 256, 512), one launch per
+                            bucket sized for its beam.  Persistent searches on one index
+                            must not overlap on the GPU (the server never uses them). */
   int32_t use_graph;     /* 1: capture the launch sequence once per call shape, then replay */
   int32_t ef_max;        /* bound on ef' over the batch when per-query ef is given; 0 => 512 */
   int32_t query_threads; /* threads per query: 32 = one warp per query (4 queries per
@@ -123,7 +125,11 @@ typedef struct {
                             verified (a multiple of 4 rows); 0 => 4 rows */
   int32_t team_lanes;    /* warp kernel: lanes sharing one row (8, 16 or 32); 0 => the
                             narrowest compiled team that covers the row */
-  int32_t reserved[2];
+  void* kernel_events;   /* NULL, or a host array of two cudaEvent_t that uhnsw_search
+                            records on its stream right before the first search-kernel
+                            launch and right after the last one: the search kernels' own
+                            duration, without the queue-ordering kernels of a persistent
+                            launch.  A CUDA-graph replay records the same two events. */
 } uhnsw_search_opts;
 
 /*

@@ -51,6 +51,7 @@ struct DevGraph {
 
 struct GraphKey {
   const void* ptr[7];
+  void* events[2];  // the handles of opts.kernel_events (opts.kernel_events itself is cleared)
   int64_t nq;
   int32_t k_max, ef_default;
   uhnsw_search_opts opts;
@@ -98,7 +99,7 @@ struct uhnsw_index {
   // exact-search workspace
   void* exact_ws = nullptr;
   size_t exact_ws_bytes = 0;
-  // bucketed persistent search: 16 counters + 16 bucket slots + the order array
+  // persistent-search queue order: bin counters and cursors, bucket slots, the order array
   int32_t* bucket_ws = nullptr;
   int64_t bucket_cap = 0;
   // autotuned launch configurations: key (ef bucket, k bucket) -> options
@@ -348,10 +349,12 @@ struct Prepared {
   size_t smem;
   int grid;
   bool persistent;
-  // bucketed persistent search (per-query ef): one launch per beam bucket,
-  // largest first, each sized for its own bucket's beam
+  // persistent search: the queue is ordered by (beam bucket, route); with
+  // per-query ef, one launch per beam bucket, largest first, each sized for
+  // its own bucket's beam
   bool bucketed = false;
   BeamBuckets bb;
+  cudaEvent_t events[2] = {nullptr, nullptr};  // opts.kernel_events, if given
   std::vector<Launch> launches;
 };
 
@@ -475,6 +478,12 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   if (P->smem > 227 * 1024)
     return fail(UHNSW_ECAPACITY, "uhnsw_search: %zu bytes of shared memory per block", P->smem);
   P->persistent = opts.persistent != 0;
+  if (opts.kernel_events) {
+    const cudaEvent_t* ev = static_cast<const cudaEvent_t*>(opts.kernel_events);
+    if (!ev[0] || !ev[1]) return fail(UHNSW_EINVAL, "uhnsw_search: kernel_events holds a NULL event");
+    P->events[0] = ev[0];
+    P->events[1] = ev[1];
+  }
   const int64_t per_block = warp ? kWarpsPerBlock : 1;
   P->grid = (int)((nq + per_block - 1) / per_block);
   if (P->persistent) {
@@ -484,14 +493,16 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
     P->grid = (int)std::min<int64_t>(P->grid, (int64_t)occ * idx->num_sms);
   }
   P->launches.clear();
-  P->bucketed = P->persistent && ef != nullptr && nq > 0;
+  P->bucketed = P->persistent && nq > 0;
   if (P->bucketed) {
-    // beam buckets <= 64, 128, 256, 512, capped at ef_cap
+    // beam buckets <= 64, 128, 256, 512, capped at ef_cap (one bucket when
+    // every query has the same ef)
     P->bb.n = 0;
-    for (int bound : {64, 128, 256, 512})
-      if (bound < ef_cap) P->bb.bound[P->bb.n++] = bound;
+    if (ef)
+      for (int bound : {64, 128, 256, 512})
+        if (bound < ef_cap) P->bb.bound[P->bb.n++] = bound;
     P->bb.bound[P->bb.n++] = ef_cap;
-    const int64_t need = 32 + nq;
+    const int64_t need = kBucketOrder + nq;
     if (need > idx->bucket_cap) {
       cudaFree(idx->bucket_ws);
       idx->bucket_ws = nullptr;
@@ -514,8 +525,8 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
       if (occ < 1) return fail(UHNSW_ECUDA, "uhnsw_search: bucket kernel does not fit");
       Lb.grid = (int)std::min<int64_t>(P->grid, (int64_t)occ * idx->num_sms);
       Lb.a.queue_head = idx->queue_head + b;
-      Lb.a.qorder = idx->bucket_ws + 32;
-      Lb.a.qbucket = idx->bucket_ws + 16 + 2 * b;
+      Lb.a.qorder = idx->bucket_ws + kBucketOrder;
+      Lb.a.qbucket = idx->bucket_ws + kBucketInfo + 2 * b;
       P->launches.push_back(Lb);
     }
   } else {
@@ -536,13 +547,22 @@ int enqueue_search(uhnsw_index* idx, const Prepared& P, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: queue reset");
   }
   if (P.bucketed) {
-    e = launch_bucketing(P.a, P.bb, idx->bucket_ws, idx->bucket_ws + 32, idx->bucket_ws + 16, st);
+    e = launch_bucketing(P.a, P.bb, idx->bucket_ws, idx->bucket_ws + kBucketOrder,
+                         idx->bucket_ws + kBucketInfo, st);
     if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: bucketing");
+  }
+  if (P.events[0]) {
+    e = cudaEventRecord(P.events[0], st);
+    if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: kernel_events[0]");
   }
   for (const Launch& L : P.launches) {
     e = P.warp ? launch_wsearch(idx->tdtype, P.wshape, L.a, L.grid, L.smem, st)
                : launch_search(idx->tdtype, P.shape, L.a, L.grid, kBlock, L.smem, st);
     if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: launch");
+  }
+  if (P.events[1]) {
+    e = cudaEventRecord(P.events[1], st);
+    if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: kernel_events[1]");
   }
   return UHNSW_OK;
 }
@@ -574,6 +594,9 @@ extern "C" int uhnsw_search(uhnsw_index* idx, const float* q, const float* p, co
   key.k_max = k_max;
   key.ef_default = ef_default;
   key.opts = *opts;
+  key.opts.kernel_events = nullptr;
+  key.events[0] = P.events[0];
+  key.events[1] = P.events[1];
   key.stream = stream;
   std::lock_guard<std::mutex> lock(idx->mu);
   for (auto& ge : idx->graphs)

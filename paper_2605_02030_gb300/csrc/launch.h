@@ -47,8 +47,14 @@ struct BeamBuckets {
   int n;
   int bound[8];
 };
-// Groups the query indices by beam bucket into `order` and writes {first
-// slot, count} per bucket into info[2b], info[2b+1] (ws: 16 int32 scratch).
+// Query routes (graph x verification p form) and sort bins (bucket x route).
+constexpr int kRoutes = 8;
+constexpr int kBins = 8 * kRoutes;
+// Bucket scratch: ws[2 kBins] counts and cursors, then info[16], then the order.
+constexpr int kBucketInfo = 2 * kBins;
+constexpr int kBucketOrder = kBucketInfo + 16;
+// Groups the query indices by beam bucket, and by route inside a bucket, into
+// `order` and writes {first slot, count} per bucket into info[2b], info[2b+1].
 cudaError_t launch_bucketing(const QueryArgs& a, const BeamBuckets& bb, int32_t* ws,
                              int32_t* order, int32_t* info, cudaStream_t st);
 

@@ -82,62 +82,81 @@ __device__ __forceinline__ int beam_bucket(const BeamBuckets& bb, int efp) {
   return bb.n - 1;  // beyond every bound: the query fails validation there
 }
 
-// Counting sort of the query indices by beam bucket: counts, then slots.
-// ws[0..8): counts, ws[8..16): cursors, info[2b] = first slot, info[2b+1] = count.
+// Code route of a query: graph (L1 / L2) and the p form of its verification
+// (none for the direct p = 1 / 2, then p = 0.5, p = 1.5, general p).  Queries
+// of one route run the same instructions, so grouping them keeps the code
+// that the warps of an SM execute at the same time small.
+__device__ __forceinline__ int query_route(float p, float cutoff) {
+  const bool direct = (p == 1.0f) || (p == 2.0f);
+  const int metric = direct ? (p == 1.0f ? 0 : 1) : (p <= cutoff ? 0 : 1);
+  const int form = direct ? 0 : p == 0.5f ? 1 : p == 1.5f ? 2 : 3;
+  return metric * 4 + form;
+}
+
+__device__ __forceinline__ int query_bin(const BeamBuckets& bb, const float* p, const int32_t* k,
+                                         const int32_t* ef, int64_t i, int k_max, int ef_default,
+                                         int t, float cutoff) {
+  const int b = beam_bucket(bb, query_beam(p[i], k ? k[i] : k_max, ef ? ef[i] : ef_default, t));
+  return b * kRoutes + query_route(p[i], cutoff);
+}
+
+// Counting sort of the query indices by (beam bucket, route): counts, then
+// slots.  ws[0..64): counts per bin, ws[64..128): cursors; info[2b] = first
+// slot of bucket b, info[2b+1] = its count.
 __global__ void bucket_count_kernel(const float* p, const int32_t* k, const int32_t* ef, int64_t nq,
-                                    int k_max, int ef_default, int t, BeamBuckets bb,
-                                    int32_t* ws) {
+                                    int k_max, int ef_default, int t, float cutoff,
+                                    BeamBuckets bb, int32_t* ws) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int b = beam_bucket(bb, query_beam(p[i], k ? k[i] : k_max, ef ? ef[i] : ef_default, t));
-    atomicAdd(&ws[b], 1);
-  }
+       i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&ws[query_bin(bb, p, k, ef, i, k_max, ef_default, t, cutoff)], 1);
 }
 
 __global__ void bucket_scatter_kernel(const float* p, const int32_t* k, const int32_t* ef,
-                                      int64_t nq, int k_max, int ef_default, int t,
+                                      int64_t nq, int k_max, int ef_default, int t, float cutoff,
                                       BeamBuckets bb, int32_t* ws, int32_t* order, int32_t* info) {
-  int base[8];
-  int acc = 0;
-  for (int b = 0; b < bb.n; ++b) {
-    base[b] = acc;
-    acc += ws[b];
-  }
   if (blockIdx.x == 0 && threadIdx.x < bb.n) {
-    info[2 * threadIdx.x] = base[threadIdx.x];
-    info[2 * threadIdx.x + 1] = ws[threadIdx.x];
+    const int b = threadIdx.x;
+    int first = 0, cnt = 0;
+    for (int j = 0; j < b * kRoutes; ++j) first += ws[j];
+    for (int j = b * kRoutes; j < (b + 1) * kRoutes; ++j) cnt += ws[j];
+    info[2 * b] = first;
+    info[2 * b + 1] = cnt;
   }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int b = beam_bucket(bb, query_beam(p[i], k ? k[i] : k_max, ef ? ef[i] : ef_default, t));
-    const int pos = atomicAdd(&ws[8 + b], 1);
-    order[base[b] + pos] = (int32_t)i;
+    const int bin = query_bin(bb, p, k, ef, i, k_max, ef_default, t, cutoff);
+    int base = 0;
+    for (int j = 0; j < bin; ++j) base += ws[j];
+    const int pos = atomicAdd(&ws[kBins + bin], 1);
+    order[base + pos] = (int32_t)i;
   }
 }
 
 cudaError_t launch_bucketing(const QueryArgs& a, const BeamBuckets& bb, int32_t* ws,
                              int32_t* order, int32_t* info, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(ws, 0, 16 * sizeof(int32_t), st);
+  cudaError_t e = cudaMemsetAsync(ws, 0, 2 * kBins * sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
   int64_t blocks = (a.nq + 255) / 256;
   if (blocks > 1024) blocks = 1024;
   bucket_count_kernel<<<(unsigned)blocks, 256, 0, st>>>(a.p, a.k, a.ef, a.nq, a.k_max,
-                                                         a.ef_default, a.t, bb, ws);
+                                                         a.ef_default, a.t, a.cutoff, bb, ws);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   bucket_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(a.p, a.k, a.ef, a.nq, a.k_max,
-                                                           a.ef_default, a.t, bb, ws, order, info);
+                                                           a.ef_default, a.t, a.cutoff, bb, ws,
+                                                           order, info);
   return cudaGetLastError();
 }
 
 bool pick_warp_shape(uhnsw_dtype dt, int chunks, int team_pref, WarpShape* out) {
-  // chosen for at most 64 registers per thread
-  static const WarpShape f32[] = {{8, 1, 4},  {16, 2, 2}, {32, 2, 2},
+  // chosen for at most 64 registers per thread; the first covering shape of
+  // each list measured fastest for 128-dimension rows (1M x 128, ef 48)
+  static const WarpShape f32[] = {{8, 1, 4},  {8, 2, 2},  {16, 2, 3}, {32, 2, 2},
                                   {32, 4, 2}, {32, 8, 1}, {32, 16, 1}};
-  static const WarpShape f16[] = {{8, 1, 4},  {8, 2, 2},  {16, 2, 2},
-                                  {32, 2, 2}, {32, 4, 2}, {32, 8, 1}};
+  static const WarpShape f16[] = {{8, 1, 4},  {8, 2, 2},  {16, 2, 2}, {32, 2, 2},
+                                  {32, 4, 2}, {32, 8, 1}, {32, 16, 1}};
   const WarpShape* list = dt == UHNSW_F32 ? f32 : f16;
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 7; ++i)
     if (list[i].team * list[i].cpl >= chunks && (team_pref == 0 || list[i].team == team_pref)) {
       *out = list[i];
       return true;

@@ -116,26 +116,22 @@ __device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
   return r;
 }
 
-// One lane's share of a base distance: the 16-byte chunks v[0..CPL) of a row
-// against the query slice q2 (pairs of FP32), accumulated as even / odd
-// element pairs.  Metric 1: sum |x - q|; metric 2: sum (x - q)^2.
-template <typename T, int CPL, int METRIC>
-__device__ __forceinline__ float lane_partial(const uint4 (&v)[CPL],
-                                              const uint64_t (&q2)[CPL][Elems16<T>::n / 2]) {
+// Elementwise |x - q| summed (metric 1) or (x - q)^2 summed (metric 2) over
+// one 16-byte chunk of a row, as even / odd element pairs accumulated into acc.
+// q holds the chunk's query values as FP32 pairs (little-endian: element 2e in
+// the low half).
+template <typename T, int METRIC>
+__device__ __forceinline__ void chunk_partial(const uint4& v, const uint64_t (&q)[Elems16<T>::n / 2],
+                                              uint64_t& acc) {
   constexpr int VEC = Elems16<T>::n;
-  uint64_t acc = 0;  // (+0.0f, +0.0f)
+  float x[VEC];
+  unpack16<T>(v, x);
 #pragma unroll
-  for (int c = 0; c < CPL; ++c) {
-    float x[VEC];
-    unpack16<T>(v[c], x);
-#pragma unroll
-    for (int e = 0; e < VEC / 2; ++e) {
-      const uint64_t df = f2_sub(f2_pack(x[2 * e], x[2 * e + 1]), q2[c][e]);
-      if (METRIC == 1) acc = f2_add(acc, df & 0x7fffffff7fffffffull);
-      else acc = f2_fma(df, df, acc);
-    }
+  for (int e = 0; e < VEC / 2; ++e) {
+    const uint64_t df = f2_sub(f2_pack(x[2 * e], x[2 * e + 1]), q[e]);
+    if (METRIC == 1) acc = f2_add(acc, df & 0x7fffffff7fffffffull);
+    else acc = f2_fma(df, df, acc);
   }
-  return f2_hsum(acc);
 }
 
 // Copies rows ids[0..nb) (row_chunks 16-byte chunks each, stride `stride`
@@ -179,12 +175,14 @@ __device__ __forceinline__ void warp_stage_rows(const T* __restrict__ rows, int 
 }
 
 // Base distances of ids[0..m) by one warp.  TEAM lanes per row, CPL 16-byte
-// chunks per lane, U rows per team loaded into registers per round.  (Staging
-// the rows in shared memory with cp.async measured slower here: it cost more
-// in occupancy than it gained in loads in flight.)
+// chunks per lane, U rows per team loaded into registers per round; the query
+// chunk is read from shared memory once per round and applied to the U rows.
+// Each row accumulates its chunks in order c = 0 .. CPL-1, elements in order,
+// then the team's lanes are summed by a butterfly.  (Staging the rows in
+// shared memory with cp.async measured slower here: it cost more in occupancy
+// than it gained in loads in flight.)
 template <typename T, int TEAM, int CPL, int U, int METRIC>
-__device__ __forceinline__ void warp_dist(const T* __restrict__ rows, int d_pad,
-                                          const uint64_t (&q2)[CPL][Elems16<T>::n / 2],
+__device__ __forceinline__ void warp_dist(const T* __restrict__ rows, int d_pad, const float* qs,
                                           const uint32_t* ids, float* out, int m, int64_t n,
                                           int32_t* err) {
   constexpr int VEC = Elems16<T>::n;
@@ -207,13 +205,26 @@ __device__ __forceinline__ void warp_dist(const T* __restrict__ rows, int d_pad,
         buf[u][c] = (ok && ch < R) ? ldg16(row + ch) : make_uint4(0u, 0u, 0u, 0u);
       }
     }
+    uint64_t acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = 0;  // (+0.0f, +0.0f)
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      const int ch = lt + c * TEAM;
+      uint64_t q[VEC / 2];
+      const uint64_t* qp = reinterpret_cast<const uint64_t*>(qs + ch * VEC);
+#pragma unroll
+      for (int e = 0; e < VEC / 2; ++e) q[e] = ch < R ? qp[e] : 0ull;
+#pragma unroll
+      for (int u = 0; u < U; ++u) chunk_partial<T, METRIC>(buf[u][c], q, acc[u]);
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      float acc = lane_partial<T, CPL, METRIC>(buf[u], q2);
+      float s = f2_hsum(acc[u]);
 #pragma unroll
-      for (int off = TEAM / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off, TEAM);
+      for (int off = TEAM / 2; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off, TEAM);
       const int i = r * NT * U + u * NT + team;
-      if (lt == 0 && i < m) out[i] = acc;
+      if (lt == 0 && i < m) out[i] = s;
     }
   }
   __syncwarp();
@@ -221,11 +232,10 @@ __device__ __forceinline__ void warp_dist(const T* __restrict__ rows, int d_pad,
 
 template <typename T, int TEAM, int CPL, int U>
 __device__ __forceinline__ void warp_dist_metric(int metric, const T* rows, int d_pad,
-                                                 const uint64_t (&q2)[CPL][Elems16<T>::n / 2],
-                                                 const uint32_t* ids, float* out, int m,
-                                                 int64_t n, int32_t* err) {
-  if (metric == 1) warp_dist<T, TEAM, CPL, U, 1>(rows, d_pad, q2, ids, out, m, n, err);
-  else warp_dist<T, TEAM, CPL, U, 2>(rows, d_pad, q2, ids, out, m, n, err);
+                                                 const float* qs, const uint32_t* ids, float* out,
+                                                 int m, int64_t n, int32_t* err) {
+  if (metric == 1) warp_dist<T, TEAM, CPL, U, 1>(rows, d_pad, qs, ids, out, m, n, err);
+  else warp_dist<T, TEAM, CPL, U, 2>(rows, d_pad, qs, ids, out, m, n, err);
 }
 
 // Drops the candidates that cannot enter a full W (those not before its last
@@ -284,11 +294,21 @@ struct WarpVerify {
   __device__ __forceinline__ uint32_t* ni_() const { return cur ? ti[0] : ti[1]; }
 };
 
-// L_p sum of a staged FP32 row (shared memory) by a team of 8 lanes, with the
-// same grouping and drop test as lp_sum_team.
+// acc + |x - q|^p over the four elements of a group, in element order.
 template <int PM>
+__device__ __forceinline__ float add_terms4(float acc, const float4& x, const float4& q, float p) {
+  acc += pow_term<PM>(fabsf(x.x - q.x), p);
+  acc += pow_term<PM>(fabsf(x.y - q.y), p);
+  acc += pow_term<PM>(fabsf(x.z - q.z), p);
+  acc += pow_term<PM>(fabsf(x.w - q.w), p);
+  return acc;
+}
+// L_p sum of a staged FP32 row (shared memory) by a team of 8 lanes, with the
+// same grouping and drop test as lp_sum_team.  The p form `pm` selects the
+// term code per 32-dimension group (a uniform branch), so that the
+// verification exists once in the kernel and not once per p form.
 __device__ __forceinline__ bool lp_sum_team_staged(const float* srow, int d, int d_pad,
-                                                   const float* qs, float p, float thr,
+                                                   const float* qs, float p, int pm, float thr,
                                                    unsigned tmask, int lane8, float& S,
                                                    int& groups) {
   float acc = 0.0f;
@@ -301,10 +321,13 @@ __device__ __forceinline__ bool lp_sum_team_staged(const float* srow, int d, int
       x = *reinterpret_cast<const float4*>(srow + j);
       qq = *reinterpret_cast<const float4*>(qs + j);
     }
-    acc += pow_term<PM>(fabsf(x.x - qq.x), p);
-    acc += pow_term<PM>(fabsf(x.y - qq.y), p);
-    acc += pow_term<PM>(fabsf(x.z - qq.z), p);
-    acc += pow_term<PM>(fabsf(x.w - qq.w), p);
+    switch (pm) {
+      case kPOne: acc = add_terms4<kPOne>(acc, x, qq, p); break;
+      case kPTwo: acc = add_terms4<kPTwo>(acc, x, qq, p); break;
+      case kPHalf: acc = add_terms4<kPHalf>(acc, x, qq, p); break;
+      case kPThreeHalves: acc = add_terms4<kPThreeHalves>(acc, x, qq, p); break;
+      default: acc = add_terms4<kPGeneral>(acc, x, qq, p); break;
+    }
     float tot = acc;
     tot += __shfl_xor_sync(tmask, tot, 1);
     tot += __shfl_xor_sync(tmask, tot, 2);
@@ -320,9 +343,8 @@ __device__ __forceinline__ bool lp_sum_team_staged(const float* srow, int d, int
 // staged candidates (8 lanes each) against the running threshold and folds
 // the finished ones into the top-k list.  With fixed_thr set, nothing is
 // dropped (the first K of Algorithm 1).
-template <int PM>
 __device__ __forceinline__ void warp_verify_range(const QueryArgs& a, const float* qs, float p,
-                                                  const uint32_t* C, int i0, int i1, int k,
+                                                  int pm, const uint32_t* C, int i0, int i1, int k,
                                                   bool no_drop, unsigned char* stage,
                                                   WarpVerify& v) {
   const int lane = threadIdx.x & 31;
@@ -340,8 +362,8 @@ __device__ __forceinline__ void warp_verify_range(const QueryArgs& a, const floa
       int groups = 0;
       if (r < nb) {
         const float* srow = reinterpret_cast<const float*>(stage) + (size_t)r * a.d_pad;
-        done = lp_sum_team_staged<PM>(srow, a.d, a.d_pad, qs, p, no_drop ? kInf : v.thr, tmask,
-                                      lane8, S, groups);
+        done = lp_sum_team_staged(srow, a.d, a.d_pad, qs, p, pm, no_drop ? kInf : v.thr, tmask,
+                                  lane8, S, groups);
       }
       const unsigned leaders = __ballot_sync(kFull, lane8 == 0 && r < nb);
       const unsigned fin = __ballot_sync(kFull, lane8 == 0 && done);
@@ -365,48 +387,36 @@ __device__ __forceinline__ void warp_verify_range(const QueryArgs& a, const floa
   }
 }
 
-template <int PM>
-__device__ void warp_verify_run(const QueryArgs& a, const float* qs, float p, const uint32_t* C,
-                                int t, int k, int kappa, bool exact, unsigned char* stage,
-                                WarpVerify& v) {
+// Exact mode verifies all of C as one range.  Algorithm 1 takes the first K
+// without a drop test, then batches of kappa until the overlap test passes.
+// One call site of warp_verify_range per p form keeps the kernel's code small.
+__device__ __forceinline__ void warp_verify_run(const QueryArgs& a, const float* qs, float p,
+                                                const uint32_t* C, int t, int k, int kappa,
+                                                bool exact, unsigned char* stage, WarpVerify& v) {
   const int lane = threadIdx.x & 31;
+  const int pm = pmode_of(p);
   v.tn = 0;
   v.thr = __int_as_float(0x7f800000);
-  if (exact || a.mode != UHNSW_VERIFY_PAPER) {
-    warp_verify_range<PM>(a, qs, p, C, 0, t, k, false, stage, v);
-    return;
-  }
-  const int n0 = min(k, t);
-  warp_verify_range<PM>(a, qs, p, C, 0, n0, k, true, stage, v);
-  int i = n0;
-  while (i < t) {
-    const int bend = min(i + kappa, t);
-    for (int j = lane; j < v.tn; j += 32) v.ci_()[j] |= kExpanded;  // mark R
-    __syncwarp();
-    warp_verify_range<PM>(a, qs, p, C, i, bend, k, false, stage, v);
+  const bool paper = !exact && a.mode == UHNSW_VERIFY_PAPER;
+  const int n0 = paper ? min(k, t) : t;
+  for (int i = 0; i < t;) {
+    const int bend = i == 0 ? n0 : min(i + kappa, t);
+    if (i > 0) {
+      for (int j = lane; j < v.tn; j += 32) v.ci_()[j] |= kExpanded;  // mark R
+      __syncwarp();
+    }
+    warp_verify_range(a, qs, p, pm, C, i, bend, k, paper && i == 0, stage, v);
+    const bool batch = i > 0;
     i = bend;
-    int ov = 0;
-    for (int j = lane; j < v.tn; j += 32) ov += (int)(v.ci_()[j] >> 31);
+    if (batch) {
+      int ov = 0;
+      for (int j = lane; j < v.tn; j += 32) ov += (int)(v.ci_()[j] >> 31);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) ov += __shfl_xor_sync(kFull, ov, off);
-    for (int j = lane; j < v.tn; j += 32) v.ci_()[j] &= kIdMask;
-    __syncwarp();
-    if ((float)ov / (float)k >= a.tau) break;
-  }
-}
-
-__device__ __forceinline__ void warp_verify_dispatch(const QueryArgs& a, const float* qs, float p,
-                                                     const uint32_t* C, int t, int k, int kappa,
-                                                     bool exact, unsigned char* stage,
-                                                     WarpVerify& v) {
-  switch (pmode_of(p)) {
-    case kPOne: warp_verify_run<kPOne>(a, qs, p, C, t, k, kappa, exact, stage, v); break;
-    case kPTwo: warp_verify_run<kPTwo>(a, qs, p, C, t, k, kappa, exact, stage, v); break;
-    case kPHalf: warp_verify_run<kPHalf>(a, qs, p, C, t, k, kappa, exact, stage, v); break;
-    case kPThreeHalves:
-      warp_verify_run<kPThreeHalves>(a, qs, p, C, t, k, kappa, exact, stage, v);
-      break;
-    default: warp_verify_run<kPGeneral>(a, qs, p, C, t, k, kappa, exact, stage, v); break;
+      for (int off = 16; off > 0; off >>= 1) ov += __shfl_xor_sync(kFull, ov, off);
+      for (int j = lane; j < v.tn; j += 32) v.ci_()[j] &= kIdMask;
+      __syncwarp();
+      if ((float)ov / (float)k >= a.tau) break;
+    }
   }
 }
 
@@ -452,167 +462,158 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
   }
   for (int j = lane; j < a.d_pad; j += 32) qs[j] = j < a.d ? a.q[qi * a.d + j] : 0.f;
   __syncwarp();
-  uint64_t q2[CPL][VEC / 2];
-  {
-    const int lt = lane % TEAM;
-#pragma unroll
-    for (int c = 0; c < CPL; ++c)
-#pragma unroll
-      for (int e = 0; e < VEC / 2; ++e) {
-        const int idx = (lt + c * TEAM) * VEC + 2 * e;
-        q2[c][e] = f2_pack(idx < a.d_pad ? qs[idx] : 0.f, idx + 1 < a.d_pad ? qs[idx + 1] : 0.f);
-      }
-  }
   const T* trav = reinterpret_cast<const T*>(a.trav);
   int nb = 1, nadj = 0, nexp = 0, nres = 0;
 
-  // greedy descent through the upper levels
-  if (lane == 0) ci[0] = (uint32_t)g.entry;
-  __syncwarp();
-  warp_dist_metric<T, TEAM, CPL, U>(metric, trav, a.d_pad, q2, ci, cd, 1, a.n, a.err);
-  int cur = g.entry;
-  float cur_d = cd[0];
-  __syncwarp();
-  for (int l = g.top_level; l >= 1; --l) {
-    for (int guard = 0; guard <= (int)min(a.n, (int64_t)INT_MAX - 1); ++guard) {
-      const int32_t row = g.up_row[chk_idx(cur, a.n, 3, a.err)];
-      if (row < 0) {
-        if (lane == 0) set_error(a.err, UHNSW_EINVAL);
-        break;
-      }
-      const int32_t* adj = g.up_adj + chk_idx((int64_t)row + l - 1, g.up_rows, 4, a.err) * g.deg;
-      int m = 0;
-      for (int b0 = 0; b0 < g.deg; b0 += 32) {
-        const int j = b0 + lane;
-        const int32_t v = j < g.deg ? adj[j] : -1;
-        warp_append(v >= 0, (uint32_t)v, ci, m, a.cmax, a.err);
-      }
-      __syncwarp();
-      nadj += 1;
-      nb += m;
-      warp_dist_metric<T, TEAM, CPL, U>(metric, trav, a.d_pad, q2, ci, cd, m, a.n, a.err);
-      float bdd = kInf;
-      int32_t bii = INT_MAX;
-      for (int i = lane; i < m; i += 32)
-        if (pair_lt(cd[i], (int32_t)ci[i], bdd, bii)) { bdd = cd[i]; bii = (int32_t)ci[i]; }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float od = __shfl_xor_sync(kFull, bdd, off);
-        const int32_t oi = __shfl_xor_sync(kFull, bii, off);
-        if (pair_lt(od, oi, bdd, bii)) { bdd = od; bii = oi; }
-      }
-      __syncwarp();
-      if (m > 0 && pair_lt(bdd, bii, cur_d, cur)) {
-        cur = bii;
-        cur_d = bdd;
-      } else {
-        break;
-      }
-    }
-  }
-
-  // layer-0 search with beam ef'
+  // One loop, one distance call site: the greedy descent through the upper
+  // levels (level >= 1), then the layer-0 search with beam ef'.  Each pass
+  // computes the base distances of the list (ci, m) gathered by the pass
+  // before: first the entry point alone, then the neighbours of the current
+  // node at `level`, then the unvisited neighbours of the expanded parents.
   const int hb = a.hash_bits;
   const int H = 1 << hb;
-  for (int j = lane; j < H; j += 32) tab[j] = kEmpty;
-  __syncwarp();
-  if (lane == 0) {
-    hash_insert(tab, hb, cur, a.err);
-    bd0[0] = cur_d;
-    bi0[0] = (uint32_t)cur;
-  }
-  __syncwarp();
-  int bn = 1, first = 0, hcount = 1;
+  const int deg0 = g.deg0;
+  const int width = a.width;
+  int level = g.top_level;
+  bool descending = true, at_entry = true;
+  int cur = g.entry;
+  float cur_d = kInf;
+  int bn = 0, first = 0, hcount = 0, m = 1;
   float* bdc = bd0;      // current W (distances / ids); the other buffer receives the merge
   uint32_t* bic = bi0;
   float* bdn = bd1;
   uint32_t* bin = bi1;
-  const int deg0 = g.deg0;
-  const int width = a.width;
-  const int64_t max_steps = a.n + 16;
-  for (int64_t step = 0; first < bn; ++step) {
+  if (lane == 0) ci[0] = (uint32_t)g.entry;
+  __syncwarp();
+  const int64_t max_steps = ((int64_t)g.top_level + 1) * (a.n + 1) + 16;
+  for (int64_t step = 0;; ++step) {
     if (step >= max_steps) {
       if (lane == 0) set_error(a.err, UHNSW_ECAPACITY);
       break;
     }
-    // parents: the first `width` unexpanded entries of W
-    int npar = 0;
+    warp_dist_metric<T, TEAM, CPL, U>(metric, trav, a.d_pad, qs, ci, cd, m, a.n, a.err);
+    if (descending) {
+      if (at_entry) {
+        cur_d = cd[0];
+        at_entry = false;
+      } else {
+        float bdd = kInf;
+        int32_t bii = INT_MAX;
+        for (int i = lane; i < m; i += 32)
+          if (pair_lt(cd[i], (int32_t)ci[i], bdd, bii)) { bdd = cd[i]; bii = (int32_t)ci[i]; }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          const float od = __shfl_xor_sync(kFull, bdd, off);
+          const int32_t oi = __shfl_xor_sync(kFull, bii, off);
+          if (pair_lt(od, oi, bdd, bii)) { bdd = od; bii = oi; }
+        }
+        __syncwarp();
+        if (m > 0 && pair_lt(bdd, bii, cur_d, cur)) {
+          cur = bii;
+          cur_d = bdd;
+        } else {
+          --level;
+        }
+      }
+      if (level >= 1) {
+        // the neighbours of cur at `level`
+        const int32_t row = g.up_row[chk_idx(cur, a.n, 3, a.err)];
+        if (row >= 0) {
+          const int32_t* adj =
+              g.up_adj + chk_idx((int64_t)row + level - 1, g.up_rows, 4, a.err) * g.deg;
+          m = 0;
+          for (int b0 = 0; b0 < g.deg; b0 += 32) {
+            const int j = b0 + lane;
+            const int32_t v = j < g.deg ? adj[j] : -1;
+            warp_append(v >= 0, (uint32_t)v, ci, m, a.cmax, a.err);
+          }
+          __syncwarp();
+          nadj += 1;
+          nb += m;
+          continue;
+        }
+        if (lane == 0) set_error(a.err, UHNSW_EINVAL);  // a node above its own level
+      }
+      // layer 0 starts from W = {cur}
+      descending = false;
+      for (int j = lane; j < H; j += 32) tab[j] = kEmpty;
+      __syncwarp();
+      if (lane == 0) {
+        hash_insert(tab, hb, cur, a.err);
+        bd0[0] = cur_d;
+        bi0[0] = (uint32_t)cur;
+      }
+      __syncwarp();
+      bn = 1;
+      first = 0;
+      hcount = 1;
+    } else {
+      // candidates behind a full W's last entry cannot enter it: drop them before sorting
+      const int mk = bn == efp
+                         ? warp_reject(cd, ci, m, bdc[bn - 1], (int32_t)(bic[bn - 1] & kIdMask))
+                         : m;
+      int nfirst;
+      const int nbn = warp_merge(bdc, bic, bn, cd, ci, mk, sd, si, bdn, bin, efp, &nfirst);
+      {
+        float* t0 = bdc;
+        bdc = bdn;
+        bdn = t0;
+        uint32_t* t1 = bic;
+        bic = bin;
+        bin = t1;
+      }
+      int hc = hcount + m;
+      if (hc > (H >> 1)) {
+        for (int j = lane; j < H; j += 32) tab[j] = kEmpty;
+        __syncwarp();
+        for (int j = lane; j < nbn; j += 32) hash_insert(tab, hb, (int32_t)(bic[j] & kIdMask), a.err);
+        __syncwarp();
+        hc = nbn;
+        ++nres;
+      }
+      bn = nbn;
+      first = nfirst;
+      hcount = hc;
+    }
+    if (first >= bn) break;
+    // Parents: the first `width` unexpanded entries of W, marked expanded.
+    // The unexpanded entry after them is most likely the next step's parent:
+    // its adjacency row is pulled toward L2 while this step runs.
+    int npar = 0, nxt = -1;
     uint32_t par_mine = 0;  // lane j < npar holds parent j
-    for (int b0 = first; b0 < bn && npar < width; b0 += 32) {
+    for (int b0 = first; b0 < bn && nxt < 0; b0 += 32) {
       const int pos = b0 + lane;
-      const bool un = pos < bn && !(bic[pos] & kExpanded);
-      const unsigned ball = __ballot_sync(kFull, un);
-      const int need = width - npar;
-      const int r = __popc(ball & lanemask_lt());
-      uint32_t pid = 0;
-      const bool take = un && r < need;
-      if (take) {
-        pid = bic[pos];
-        bic[pos] = pid | kExpanded;
+      unsigned ball = __ballot_sync(kFull, pos < bn && !(bic[pos] & kExpanded));
+      while (ball && npar < width) {
+        const int src = __ffs(ball) - 1;
+        const uint32_t v = bic[b0 + src];
+        __syncwarp();
+        if (lane == npar) par_mine = v;
+        if (lane == src) bic[pos] = v | kExpanded;
+        ball &= ball - 1;
+        ++npar;
       }
-      // move each taken id to lane npar + r
-      const unsigned takers = __ballot_sync(kFull, take);
-      for (int s = 0; s < min(__popc(ball), need); ++s) {
-        const int src = __fns(takers, 0, s + 1);
-        const uint32_t v = __shfl_sync(kFull, pid, src);
-        if (lane == npar + s) par_mine = v;
-      }
-      npar += min(__popc(ball), need);
+      if (ball) nxt = (int)bic[b0 + __ffs(ball) - 1];
     }
-    // The next step most likely expands the next unexpanded entry of W: pull
-    // its adjacency row toward L2 while this step runs.
-    {
-      int nxt = -1;
-      for (int b0 = first; b0 < bn && nxt < 0; b0 += 32) {
-        const int pos = b0 + lane;
-        const unsigned un = __ballot_sync(kFull, pos < bn && !(bic[pos] & kExpanded));
-        if (un) nxt = __shfl_sync(kFull, (int)bic[min(b0 + __ffs(un) - 1, bn - 1)], 0);
-      }
-      if (nxt >= 0 && lane < (deg0 * 4 + 127) / 128)
-        prefetch_l2(g.ell0 + chk_idx(nxt, a.n, 5, a.err) * deg0 + lane * 32);
-    }
+    if (nxt >= 0 && lane < (deg0 * 4 + 127) / 128)
+      prefetch_l2(g.ell0 + chk_idx(nxt, a.n, 5, a.err) * deg0 + lane * 32);
     __syncwarp();
-    const int total = npar * deg0;
-    int m = 0;
-    for (int b0 = 0; b0 < total; b0 += 32) {
-      const int j = b0 + lane;
-      const int pj = j / deg0;
-      const uint32_t parent = __shfl_sync(kFull, par_mine, pj < 32 ? pj : 0);
-      int32_t v = -1;
-      if (j < total) v = g.ell0[chk_idx(parent, a.n, 5, a.err) * deg0 + (j % deg0)];
-      const bool fresh = v >= 0 && hash_insert(tab, hb, v, a.err);
-      warp_append(fresh, (uint32_t)v, ci, m, a.cmax, a.err);
+    // the unvisited neighbours of the parents, in parent order
+    m = 0;
+    for (int s = 0; s < npar; ++s) {
+      const uint32_t parent = __shfl_sync(kFull, par_mine, s);
+      const int32_t* adj = g.ell0 + chk_idx(parent, a.n, 5, a.err) * deg0;
+      for (int b0 = 0; b0 < deg0; b0 += 32) {
+        const int j = b0 + lane;
+        const int32_t v = j < deg0 ? adj[j] : -1;
+        const bool fresh = v >= 0 && hash_insert(tab, hb, v, a.err);
+        warp_append(fresh, (uint32_t)v, ci, m, a.cmax, a.err);
+      }
     }
     __syncwarp();
     nexp += npar;
     nadj += npar;
     nb += m;
-    warp_dist_metric<T, TEAM, CPL, U>(metric, trav, a.d_pad, q2, ci, cd, m, a.n, a.err);
-    // candidates behind a full W's last entry cannot enter it: drop them before sorting
-    const int mk = bn == efp ? warp_reject(cd, ci, m, bdc[bn - 1], (int32_t)(bic[bn - 1] & kIdMask))
-                             : m;
-    int nfirst;
-    const int nbn = warp_merge(bdc, bic, bn, cd, ci, mk, sd, si, bdn, bin, efp, &nfirst);
-    {
-      float* t0 = bdc;
-      bdc = bdn;
-      bdn = t0;
-      uint32_t* t1 = bic;
-      bic = bin;
-      bin = t1;
-    }
-    int hc = hcount + m;
-    if (hc > (H >> 1)) {
-      for (int j = lane; j < H; j += 32) tab[j] = kEmpty;
-      __syncwarp();
-      for (int j = lane; j < nbn; j += 32) hash_insert(tab, hb, (int32_t)(bic[j] & kIdMask), a.err);
-      __syncwarp();
-      hc = nbn;
-      ++nres;
-    }
-    bn = nbn;
-    first = nfirst;
-    hcount = hc;
   }
 
   // p in {1, 2} returns the beam's first k directly when the beam ran on the
@@ -645,7 +646,7 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
   v.sd = sd;
   v.si = si;
   const int kappa = a.kappa > 0 ? a.kappa : k;
-  warp_verify_dispatch(a, qs, p, bic, nc, k, kappa, direct, stage, v);
+  warp_verify_run(a, qs, p, bic, nc, k, kappa, direct, stage, v);
   const double inv_p = 1.0 / (double)p;
   for (int j = lane; j < a.k_max; j += 32) {
     if (j < k && j < v.tn) {

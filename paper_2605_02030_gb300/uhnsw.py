@@ -62,7 +62,7 @@ class _SearchOpts(C.Structure):
         ("stats", C.c_void_p),
         ("stage_bytes", C.c_int32),
         ("team_lanes", C.c_int32),
-        ("reserved", C.c_int32 * 2),
+        ("kernel_events", C.c_void_p),
     ]
 
 
@@ -263,10 +263,12 @@ class Index:
                kappa: int = 0, cutoff: float = 0.0, mode: str = "exact", width: int = 1,
                persistent: bool = False, use_graph: bool = False, ef_max: int = 0,
                query_threads: int = 0, stage_bytes: int = 0, team_lanes: int = 0,
-               stats: bool = False, out=None, stream=None):
+               stats: bool = False, out=None, stream=None, kernel_events=None):
         """Algorithm 1 on device tensors.  q: float32 [nq, d] cuda; p: float32 [nq];
-        k / ef: int (same for all) or int32 [nq] tensors.  Returns (ids int64
-        [nq, k_max], dist float32 [nq, k_max], stats int32 [nq, 8] or None)."""
+        k / ef: int (same for all) or int32 [nq] tensors.  kernel_events: two
+        torch.cuda.Event (already recorded once) bracketing the search kernels
+        alone.  Returns (ids int64 [nq, k_max], dist float32 [nq, k_max], stats
+        int32 [nq, 8] or None)."""
         import torch
         lib = load_library()
         nq = q.shape[0]
@@ -286,6 +288,11 @@ class Index:
         st = torch.zeros((nq, NSTATS), dtype=torch.int32, device=q.device) if stats else None
         o = self._opts(t, kappa, tau, cutoff, mode, width, persistent, use_graph, ef_max, st,
                        query_threads, stage_bytes, team_lanes)
+        if kernel_events is not None:
+            evs = (C.c_void_p * 2)(*(int(e.cuda_event) for e in kernel_events))
+            if not evs[0] or not evs[1]:
+                raise ValueError("kernel_events: record each event once before passing it")
+            o.kernel_events = C.cast(evs, C.c_void_p)
         _check(lib.uhnsw_search(self._h, _t_ptr(q), _t_ptr(p), _t_ptr(k_t), _t_ptr(ef_t), nq,
                                 k_max, ef_default, C.byref(o), _t_ptr(ids), _t_ptr(dist),
                                 _stream_ptr(stream)))

@@ -384,3 +384,35 @@ def test_bucketed_persistent_queue_matches_plain(U, search_case, qt):
     assert (b[2].cpu().numpy()[:, 5] == 0).all()
     assert idx.device_status() == 0
     idx.close()
+
+
+def test_queue_route_order_and_kernel_events(U, search_case, qt):
+    """The persistent queue ordered by (beam bucket, route) returns what the
+    plain launch returns for a mix of routes (G1 / G2, direct p, p = 0.5 and
+    1.5, general p), and the kernel_events option brackets the search kernels
+    without changing any result, plain and under CUDA-graph replay."""
+    cname, w, base, qs, p, g1, g2 = search_case
+    nq = len(qs)
+    pr = np.resize(np.array([1.0, 2.0, 0.5, 1.5, 0.7, 1.3, 1.8, 1.4], np.float32), nq)
+    np.random.default_rng(4).shuffle(pr)
+    idx = U.Index(base, g1, g2, traverse_dtype="f16")
+    a = idx.search(dev(qs), dev(pr), k=10, ef=32, query_threads=qt, stats=True)
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    for e in ev:
+        e.record()
+    for graph in (False, True):
+        for _ in range(2):
+            b = idx.search(dev(qs), dev(pr), k=10, ef=32, query_threads=qt, persistent=True,
+                           use_graph=graph, kernel_events=ev)
+            torch.cuda.synchronize()
+            assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+            assert ev[0].elapsed_time(ev[1]) > 0.0
+    st = a[2].cpu().numpy()
+    assert (st[:, 5] == 0).all()
+    assert set(np.unique(st[:, 6]).tolist()) == {1, 2}
+    bad = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    if int(bad[0].cuda_event) == 0:                  # torch creates events at first record
+        with pytest.raises(ValueError):
+            idx.search(dev(qs), dev(pr), k=10, ef=32, kernel_events=bad)
+    assert idx.device_status() == 0
+    idx.close()
