@@ -118,8 +118,11 @@ typedef struct {
   int32_t use_graph;     /* 1: capture the launch sequence once per call shape, then replay */
   int32_t ef_max;        /* bound on ef' over the batch when per-query ef is given; 0 => 512 */
   int32_t query_threads; /* threads per query: 32 = one warp per query (4 queries per
-                            block), 128 = one block per query; 0 => the configuration
-                            uhnsw_autotune chose for this beam / k bucket, else 32 */
+                            block), 128 = one block per query; a launch that does not fit
+                            in shared memory fails with UHNSW_ECAPACITY.  0 => the
+                            configuration uhnsw_autotune chose for this beam / k bucket,
+                            else 32; then a beam bucket whose warp-kernel layout does not
+                            fit runs the block kernel. */
   int32_t* stats;        /* device [nq][UHNSW_NSTATS] int32, or NULL */
   int32_t stage_bytes;   /* warp kernel: shared memory per query for the FP32 rows being
                             verified (a multiple of 4 rows); 0 => 4 rows */
@@ -129,7 +132,7 @@ typedef struct {
                             records on its stream right before the first search-kernel
                             launch and right after the last one: the search kernels' own
                             duration, without the queue-ordering kernels of a persistent
-                            launch.  A CUDA-graph replay records the same two events. */
+                            launch.  Such a call runs without CUDA-graph replay. */
 } uhnsw_search_opts;
 
 /*

@@ -51,7 +51,6 @@ struct DevGraph {
 
 struct GraphKey {
   const void* ptr[7];
-  void* events[2];  // the handles of opts.kernel_events (opts.kernel_events itself is cleared)
   int64_t nq;
   int32_t k_max, ef_default;
   uhnsw_search_opts opts;
@@ -337,6 +336,7 @@ namespace {
 
 struct Launch {
   QueryArgs a;
+  bool warp;     // warp-per-query kernel, else block-per-query
   size_t smem;
   int grid;
 };
@@ -345,9 +345,6 @@ struct Prepared {
   QueryArgs a;
   TeamShape shape;    // block-per-query kernel
   WarpShape wshape;   // warp-per-query kernel
-  bool warp;
-  size_t smem;
-  int grid;
   bool persistent;
   // persistent search: the queue is ordered by (beam bucket, route); with
   // per-query ef, one launch per beam bucket, largest first, each sized for
@@ -397,6 +394,10 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   else ef_cap = std::max({ef_default, opts.t, k_max});
   if (ef_cap > UHNSW_MAX_EF)
     return fail(UHNSW_EINVAL, "uhnsw_search: beam %d exceeds %d", ef_cap, UHNSW_MAX_EF);
+  // query_threads given by the caller is binding; otherwise (0, or the
+  // autotuned choice) a beam bucket whose warp-kernel layout does not fit in
+  // shared memory runs the block kernel instead
+  const bool forced = opts.query_threads != 0;
   if (opts.query_threads == 0) {
     // the autotuned configuration of this bucket, if any
     const int64_t key = ((int64_t)(1 << next_pow2_bits(ef_cap)) << 16) | (1 << next_pow2_bits(k_max));
@@ -416,25 +417,21 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
       deg0 = std::max(deg0, G.deg0);
       deg = std::max(deg, G.deg);
     }
-  const bool warp = opts.query_threads != kBlock;
-  const int cmax = std::max({width * deg0, deg, warp ? 4 : kBlock / 8});
-  int hb = next_pow2_bits(4ll * (ef_cap + width * deg0));
-  hb = std::max(hb, 9);
-  if (hb > 15) return fail(UHNSW_ECAPACITY, "uhnsw_search: visited table too large");
-  // warp kernel: rows are staged in batches of sb (traversal) and sv (FP32
-  // verification, a multiple of the 4 teams of a warp)
-  int sb = 0, sv = 0, stage = 0;
-  if (warp) {
-    const int vrow = idx->d_pad * 4;
-    sv = std::max(4, (opts.stage_bytes > 0 ? opts.stage_bytes / vrow : 4) & ~3);
-    stage = sv * vrow;
-  }
-  const SmemLayout L(idx->d_pad, ef_cap, hb, cmax, k_max, 0, stage);
+  const bool want_warp = opts.query_threads != kBlock;
+  if (next_pow2_bits(4ll * (ef_cap + width * deg0)) > 15)
+    return fail(UHNSW_ECAPACITY, "uhnsw_search: visited table too large");
   const int chunks = idx->d_pad / (idx->tdtype == UHNSW_F32 ? 4 : 8);
   TeamShape sh{0, 0};
   WarpShape wsh{0, 0, 0};
-  if (warp ? !pick_warp_shape(idx->tdtype, chunks, opts.team_lanes, &wsh) : !pick_shape(idx->tdtype, chunks, &sh))
+  const bool have_block = pick_shape(idx->tdtype, chunks, &sh);
+  const bool have_warp = pick_warp_shape(idx->tdtype, chunks, opts.team_lanes, &wsh);
+  if (want_warp ? !have_warp : !have_block)
     return fail(UHNSW_ECAPACITY, "uhnsw_search: no kernel shape for d=%d", idx->d);
+  // warp kernel: the FP32 rows being verified are staged sv at a time (a
+  // multiple of the 4 teams of a warp)
+  const int vrow = idx->d_pad * 4;
+  const int sv = std::max(4, (opts.stage_bytes > 0 ? opts.stage_bytes / vrow : 4) & ~3);
+  constexpr size_t kSmemMax = 227 * 1024;
 
   QueryArgs& a = P->a;
   std::memset(&a, 0, sizeof(a));
@@ -459,8 +456,6 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   a.cutoff = opts.cutoff > 0.f ? opts.cutoff : 1.4f;
   a.mode = opts.verify_mode;
   a.width = width;
-  a.hash_bits = hb;
-  a.cmax = cmax;
   a.vcap = 0;
   a.out_ids = out_ids;
   a.out_dist = out_dist;
@@ -468,15 +463,9 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   a.err = idx->err;
   a.trav_exact = idx->trav_exact ? 1 : 0;
   a.queue_head = opts.persistent ? idx->queue_head : nullptr;
-  a.stage_bytes = stage;
-  a.sb = sb;
-  a.sv = sv;
+  a.sb = 0;
   P->shape = sh;
   P->wshape = wsh;
-  P->warp = warp;
-  P->smem = warp ? (size_t)L.total * kWarpsPerBlock : (size_t)L.total;
-  if (P->smem > 227 * 1024)
-    return fail(UHNSW_ECAPACITY, "uhnsw_search: %zu bytes of shared memory per block", P->smem);
   P->persistent = opts.persistent != 0;
   if (opts.kernel_events) {
     const cudaEvent_t* ev = static_cast<const cudaEvent_t*>(opts.kernel_events);
@@ -484,14 +473,41 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
     P->events[0] = ev[0];
     P->events[1] = ev[1];
   }
-  const int64_t per_block = warp ? kWarpsPerBlock : 1;
-  P->grid = (int)((nq + per_block - 1) / per_block);
-  if (P->persistent) {
-    const int occ = warp ? wsearch_occupancy(idx->tdtype, wsh, P->smem)
-                         : search_occupancy(idx->tdtype, sh, kBlock, P->smem);
-    if (occ < 1) return fail(UHNSW_ECUDA, "uhnsw_search: kernel does not fit (smem %zu)", P->smem);
-    P->grid = (int)std::min<int64_t>(P->grid, (int64_t)occ * idx->num_sms);
-  }
+
+  // One launch description for a beam bound: kernel kind, layout, grid.
+  auto describe = [&](int bound, Launch* Lo) -> int {
+    Lo->a = a;
+    Lo->a.ef_cap = bound;
+    Lo->a.hash_bits = std::max(9, next_pow2_bits(4ll * (bound + width * deg0)));
+    bool w = want_warp;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      const int cmax = std::max({width * deg0, deg, w ? 4 : kBlock / 8});
+      const int stage = w ? sv * vrow : 0;
+      const SmemLayout Lw(idx->d_pad, bound, Lo->a.hash_bits, cmax, k_max, 0, stage);
+      const size_t smem = w ? (size_t)Lw.total * kWarpsPerBlock : (size_t)Lw.total;
+      if (smem <= kSmemMax) {
+        Lo->warp = w;
+        Lo->smem = smem;
+        Lo->a.cmax = cmax;
+        Lo->a.stage_bytes = stage;
+        Lo->a.sv = w ? sv : 0;
+        const int64_t per_block = w ? kWarpsPerBlock : 1;
+        Lo->grid = (int)((nq + per_block - 1) / per_block);
+        if (P->persistent) {
+          const int occ = w ? wsearch_occupancy(idx->tdtype, wsh, smem)
+                            : search_occupancy(idx->tdtype, sh, kBlock, smem);
+          if (occ < 1) return fail(UHNSW_ECUDA, "uhnsw_search: kernel does not fit (smem %zu)", smem);
+          Lo->grid = (int)std::min<int64_t>(Lo->grid, (int64_t)occ * idx->num_sms);
+        }
+        return UHNSW_OK;
+      }
+      if (!w || forced || !have_block)
+        return fail(UHNSW_ECAPACITY, "uhnsw_search: %zu bytes of shared memory per block", smem);
+      w = false;  // the block kernel holds one query per block
+    }
+    return fail(UHNSW_ECAPACITY, "uhnsw_search: no launch fits");
+  };
+
   P->launches.clear();
   P->bucketed = P->persistent && nq > 0;
   if (P->bucketed) {
@@ -513,17 +529,8 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
     }
     for (int b = P->bb.n - 1; b >= 0; --b) {
       Launch Lb;
-      Lb.a = a;
-      const int bound = P->bb.bound[b];
-      Lb.a.ef_cap = bound;
-      int bhb = std::max(9, next_pow2_bits(4ll * (bound + width * deg0)));
-      Lb.a.hash_bits = bhb;
-      const SmemLayout Lw(idx->d_pad, bound, bhb, cmax, k_max, 0, stage);
-      Lb.smem = warp ? (size_t)Lw.total * kWarpsPerBlock : (size_t)Lw.total;
-      const int occ = warp ? wsearch_occupancy(idx->tdtype, wsh, Lb.smem)
-                           : search_occupancy(idx->tdtype, sh, kBlock, Lb.smem);
-      if (occ < 1) return fail(UHNSW_ECUDA, "uhnsw_search: bucket kernel does not fit");
-      Lb.grid = (int)std::min<int64_t>(P->grid, (int64_t)occ * idx->num_sms);
+      const int rc = describe(P->bb.bound[b], &Lb);
+      if (rc != UHNSW_OK) return rc;
       Lb.a.queue_head = idx->queue_head + b;
       Lb.a.qorder = idx->bucket_ws + kBucketOrder;
       Lb.a.qbucket = idx->bucket_ws + kBucketInfo + 2 * b;
@@ -531,11 +538,11 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
     }
   } else {
     Launch L1;
-    L1.a = a;
-    L1.smem = P->smem;
-    L1.grid = P->grid;
+    const int rc = describe(ef_cap, &L1);
+    if (rc != UHNSW_OK) return rc;
     P->launches.push_back(L1);
   }
+  P->a = P->launches.front().a;
   return UHNSW_OK;
 }
 
@@ -556,7 +563,7 @@ int enqueue_search(uhnsw_index* idx, const Prepared& P, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: kernel_events[0]");
   }
   for (const Launch& L : P.launches) {
-    e = P.warp ? launch_wsearch(idx->tdtype, P.wshape, L.a, L.grid, L.smem, st)
+    e = L.warp ? launch_wsearch(idx->tdtype, P.wshape, L.a, L.grid, L.smem, st)
                : launch_search(idx->tdtype, P.shape, L.a, L.grid, kBlock, L.smem, st);
     if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: launch");
   }
@@ -578,7 +585,10 @@ extern "C" int uhnsw_search(uhnsw_index* idx, const float* q, const float* p, co
   int rc = prepare_search(idx, q, p, k, ef, nq, k_max, ef_default, opts, out_ids, out_dist, &P);
   if (rc != UHNSW_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  if (!opts || !opts->use_graph || nq == 0) return enqueue_search(idx, P, st);
+  // A plain cudaEventRecord inside a stream capture only marks a dependency
+  // (it records nothing when the graph runs), so timed calls skip the graph.
+  if (!opts || !opts->use_graph || opts->kernel_events || nq == 0)
+    return enqueue_search(idx, P, st);
 
   // CUDA-graph path: capture the launch sequence once per call shape, replay.
   GraphKey key;
@@ -594,9 +604,6 @@ extern "C" int uhnsw_search(uhnsw_index* idx, const float* q, const float* p, co
   key.k_max = k_max;
   key.ef_default = ef_default;
   key.opts = *opts;
-  key.opts.kernel_events = nullptr;
-  key.events[0] = P.events[0];
-  key.events[1] = P.events[1];
   key.stream = stream;
   std::lock_guard<std::mutex> lock(idx->mu);
   for (auto& ge : idx->graphs)
@@ -890,6 +897,11 @@ extern "C" int uhnsw_autotune(uhnsw_index* idx, const float* q, const float* p, 
       if (rc == UHNSW_OK && e != cudaSuccess) rc = cuda_fail(e, "uhnsw_autotune: run");
       if (rc == UHNSW_OK && r > 0) cudaEventElapsedTime(&ts[r - 1], e0, e1);
     }
+    if (rc == UHNSW_ECAPACITY) {  // this configuration does not fit: skip it
+      clear_error();
+      rc = UHNSW_OK;
+      continue;
+    }
     if (rc != UHNSW_OK) break;
     std::sort(ts, ts + 3);
     if (ts[1] < best_t) {
@@ -902,6 +914,7 @@ extern "C" int uhnsw_autotune(uhnsw_index* idx, const float* q, const float* p, 
   cudaFree(ids);
   cudaFree(dist);
   if (rc != UHNSW_OK) return rc;
+  if (best_i < 0) return fail(UHNSW_ECAPACITY, "uhnsw_autotune: no configuration fits");
   const int64_t key = ((int64_t)(1 << next_pow2_bits(efp)) << 16) | (1 << next_pow2_bits(k));
   {
     std::lock_guard<std::mutex> lock(idx->tuned_mu);

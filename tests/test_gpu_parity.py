@@ -416,3 +416,24 @@ def test_queue_route_order_and_kernel_events(U, search_case, qt):
             idx.search(dev(qs), dev(pr), k=10, ef=32, kernel_events=bad)
     assert idx.device_status() == 0
     idx.close()
+
+
+def test_large_beam_buckets_fall_back_to_the_block_kernel(U):
+    """A beam bucket too large for four warp-kernel queries per block runs the
+    block kernel when query_threads is left to the library, and returns what
+    the block kernel alone returns; forcing the warp kernel fails cleanly."""
+    w, base, qs, p, _, _ = workload_arrays("mixture10k", 3000, 40, 1 / 16)
+    g1, g2 = oracle_graphs("mixture10k", 3000, 40, 1 / 16)
+    idx = U.Index(base, g1, g2, traverse_dtype="f32")
+    ef = np.where(np.arange(len(qs)) % 2 == 0, 32, 500).astype(np.int32)
+    # 256 staged rows: the ef <= 64 bucket fits four warp queries per block
+    # (141 KB), the ef 512 bucket does not (233 KB > 227 KB)
+    kw = dict(k=10, ef=dev(ef), k_max=10, ef_max=512, stage_bytes=32768)
+    a = idx.search(dev(qs), dev(p), persistent=True, **kw)
+    b = idx.search(dev(qs), dev(p), query_threads=128, **kw)
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    with pytest.raises(U.UHNSWError):
+        idx.search(dev(qs), dev(p), query_threads=32, **kw)
+    assert idx.device_status() == 0
+    idx.close()
