@@ -191,18 +191,23 @@ __device__ __forceinline__ void warp_dist(const T* __restrict__ rows, int d_pad,
   const int team = lane / TEAM, lt = lane % TEAM;
   const int R = d_pad / VEC;
   const int rounds = (m + NT * U - 1) / (NT * U);
+  // A row of exactly TEAM * CPL chunks needs no chunk bounds; otherwise the
+  // chunks past the row read the row's last chunk and are zeroed (no branch
+  // around the loads).  Rows past m repeat the last candidate's row (already
+  // in flight, so no extra DRAM traffic) and their sums are not written.
+  const bool cover = TEAM * CPL == R;
   for (int r = 0; r < rounds; ++r) {
     uint4 buf[U][CPL];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int i = r * NT * U + u * NT + team;
-      const bool ok = i < m;
-      const int64_t id = ok ? chk_idx((int64_t)(ids[i] & kIdMask), n, 1, err) : 0;
+      const int i = min(r * NT * U + u * NT + team, m - 1);
+      const int64_t id = chk_idx((int64_t)(ids[i] & kIdMask), n, 1, err);
       const uint4* row = reinterpret_cast<const uint4*>(rows + id * d_pad);
 #pragma unroll
       for (int c = 0; c < CPL; ++c) {
         const int ch = lt + c * TEAM;
-        buf[u][c] = (ok && ch < R) ? ldg16(row + ch) : make_uint4(0u, 0u, 0u, 0u);
+        buf[u][c] = __ldg(row + (cover ? ch : min(ch, R - 1)));
+        if (!cover && ch >= R) buf[u][c] = make_uint4(0u, 0u, 0u, 0u);
       }
     }
     uint64_t acc[U];
@@ -212,9 +217,17 @@ __device__ __forceinline__ void warp_dist(const T* __restrict__ rows, int d_pad,
     for (int c = 0; c < CPL; ++c) {
       const int ch = lt + c * TEAM;
       uint64_t q[VEC / 2];
-      const uint64_t* qp = reinterpret_cast<const uint64_t*>(qs + ch * VEC);
+      const ulonglong2* qp = reinterpret_cast<const ulonglong2*>(qs + (cover ? ch : min(ch, R - 1)) * VEC);
 #pragma unroll
-      for (int e = 0; e < VEC / 2; ++e) q[e] = ch < R ? qp[e] : 0ull;
+      for (int e = 0; e < VEC / 4; ++e) {
+        const ulonglong2 v = qp[e];
+        q[2 * e] = v.x;
+        q[2 * e + 1] = v.y;
+      }
+      if (!cover && ch >= R) {
+#pragma unroll
+        for (int e = 0; e < VEC / 2; ++e) q[e] = 0ull;
+      }
 #pragma unroll
       for (int u = 0; u < U; ++u) chunk_partial<T, METRIC>(buf[u][c], q, acc[u]);
     }
@@ -423,7 +436,6 @@ __device__ __forceinline__ void warp_verify_run(const QueryArgs& a, const float*
 // ---------------------------------------------------------------- one query (warp)
 template <typename T, int TEAM, int CPL, int U>
 __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, const SmemLayout& L) {
-  constexpr int VEC = Elems16<T>::n;
   const int lane = threadIdx.x & 31;
   const float kInf = __int_as_float(0x7f800000);
   unsigned char* stage = ws + L.stage;
