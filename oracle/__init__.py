@@ -84,9 +84,9 @@ def _load():
     lib.oracle_verify_paper.argtypes = [P, C.c_int32, P, C.c_double, P, C.c_int32, C.c_int32,
                                         C.c_int32, C.c_float, P, P, P, P]
     lib.oracle_uhnsw_query.restype = C.c_int
-    lib.oracle_uhnsw_query.argtypes = [C.POINTER(_CSR), C.POINTER(_CSR), P, C.c_int32, P, C.c_float,
-                                       C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_int32,
-                                       C.c_float, C.c_int32, P, P, P]
+    lib.oracle_uhnsw_query.argtypes = [C.POINTER(_CSR), C.POINTER(_CSR), C.c_int32, C.c_int32, P,
+                                       C.c_int32, P, C.c_float, C.c_int32, C.c_int32, C.c_int32,
+                                       C.c_float, C.c_int32, C.c_float, C.c_int32, P, P, P]
     _lib = lib
     return lib
 
@@ -106,8 +106,15 @@ def lp_sum(x, q, p: float) -> float:
     return _load().oracle_lp_sum(_ptr(x), _ptr(q), x.shape[-1], float(p))
 
 
+# Base metrics of the graphs (metric codes): 1 = L1, sum |d_j|; 2 = squared
+# L2, sum d_j^2; 3 = L0.5 without its root, sum |d_j|^(1/2).  METRIC_P is the
+# p of each.  U-HNSW uses G1 (L1) and G2 (L2) with cutoff 1.4; U-HNSW-E
+# (Section 4.6) uses G0.5 (L0.5) and G1 (L1) with cutoff 0.6.
+METRIC_P = {1: 1.0, 2: 2.0, 3: 0.5}
+
+
 def base_dist(x, q, metric: int) -> float:
-    """metric 1: sum |d_j| (L1); metric 2: sum d_j^2 (squared L2)."""
+    """metric 1: sum |d_j| (L1); 2: sum d_j^2 (squared L2); 3: sum |d_j|^(1/2) (L0.5)."""
     x, q = _f32(x), _f32(q)
     return _load().oracle_base_dist(_ptr(x), _ptr(q), x.shape[-1], int(metric))
 
@@ -141,7 +148,7 @@ def select_heuristic(base, cand, cand_d, m: int, metric: int):
 
 
 def hnsw_build(base, metric: int, M: int, ef_construction: int, levels, M0: int | None = None):
-    """HNSW graph under L1 (metric=1) or L2 (metric=2), as a CSR dict:
+    """HNSW graph under L1 (metric=1), L2 (metric=2) or L0.5 (metric=3), as a CSR dict:
     {num_levels, entry_point, max_degree0, max_degree, n,
      levels: [{nodes int32, offsets int64, nbrs int32}, ...]} (level 0 nodes = all ids)."""
     base = _f32(base)
@@ -247,23 +254,27 @@ def verify_paper(base, q, p: float, cand, k: int, kappa: int, tau: float):
 
 # ---------------------------------------------------------------- Algorithm 1
 def uhnsw_query(g1, g2, base, q, p: float, k: int, ef: int, t: int = 0, tau: float = 0.92,
-                kappa: int = 0, cutoff: float = 1.4, mode: int = 0, _holders=None):
-    """One query of Algorithm 1: (ids int64 [k], dist float64 [k], stats [N_b, N_p, terms])."""
+                kappa: int = 0, cutoff: float = 1.4, mode: int = 0, metrics=(1, 2), _holders=None):
+    """One query of Algorithm 1: (ids int64 [k], dist float64 [k], stats [N_b, N_p, terms]).
+    g1 / g2 are the graphs routed for p <= cutoff / p > cutoff, under the base
+    metrics `metrics` (U-HNSW: (1, 2); U-HNSW-E: (3, 1) with cutoff 0.6)."""
     base, q = _f32(base), _f32(q)
     h1 = _holders[0] if _holders else _CSRHolder(g1)
     h2 = _holders[1] if _holders else _CSRHolder(g2)
     ids = np.empty(k, np.int64)
     dist = np.empty(k, np.float64)
     st = np.zeros(3, np.int64)
-    rc = _load().oracle_uhnsw_query(C.byref(h1.s), C.byref(h2.s), _ptr(base), base.shape[1], _ptr(q),
-                                    float(p), k, ef, t, float(tau), kappa, float(cutoff), mode,
-                                    _ptr(ids), _ptr(dist), _ptr(st))
+    rc = _load().oracle_uhnsw_query(C.byref(h1.s), C.byref(h2.s), int(metrics[0]), int(metrics[1]),
+                                    _ptr(base), base.shape[1], _ptr(q), float(p), k, ef, t,
+                                    float(tau), kappa, float(cutoff), mode, _ptr(ids), _ptr(dist),
+                                    _ptr(st))
     if rc != 0:
         raise ValueError(f"oracle_uhnsw_query: {rc}")
     return ids, dist, st
 
 
-def uhnsw_batch(g1, g2, base, queries, p, k, ef, t=0, tau=0.92, kappa=0, cutoff=1.4, mode=0):
+def uhnsw_batch(g1, g2, base, queries, p, k, ef, t=0, tau=0.92, kappa=0, cutoff=1.4, mode=0,
+                metrics=(1, 2)):
     """Algorithm 1 over a batch (per-query p, k, ef arrays or scalars).
     Returns ids int64 [nq, kmax] and dist float64 [nq, kmax] (-1 / inf padded)."""
     queries = _f32(queries)
@@ -278,7 +289,7 @@ def uhnsw_batch(g1, g2, base, queries, p, k, ef, t=0, tau=0.92, kappa=0, cutoff=
     stats = np.zeros((nq, 3), np.int64)
     for i in range(nq):
         a, b, s = uhnsw_query(g1, g2, base, queries[i], float(p[i]), int(k[i]), int(ef[i]), t, tau,
-                              kappa, cutoff, mode, _holders=holders)
+                              kappa, cutoff, mode, metrics, _holders=holders)
         ids[i, :k[i]] = a
         dist[i, :k[i]] = b
         stats[i] = s

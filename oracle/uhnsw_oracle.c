@@ -29,11 +29,15 @@
  *                         |R_new ∩ R| / K >= tau early stop (Section 3.1)
  *   oracle_uhnsw_query    Algorithm 1 end to end, with the p <= cutoff
  *                         routing (Section 3.1) and the direct K-NN for
- *                         p in {1, 2} (Section 3 introduction)
+ *                         p in {1, 2} (Section 3 introduction); with graphs
+ *                         under L0.5 and L1 and cutoff 0.6 it is U-HNSW-E
+ *                         (Section 4.6), whose direct K-NN is for p in
+ *                         {0.5, 1}
  *
  * Order used everywhere: lexicographic (distance, id), ids ascending on ties.
- * Base metric of G1 is sum |d_j| (L1); of G2 the squared L2 sum d_j^2, which
- * orders points exactly like L2.
+ * Base metrics (metric codes): 1 = L1, sum |d_j|; 2 = the squared L2 sum
+ * d_j^2, which orders points exactly like L2; 3 = L0.5 without its root,
+ * sum |d_j|^(1/2), which orders points exactly like L0.5.
  */
 #include <math.h>
 #include <stdint.h>
@@ -58,16 +62,24 @@ double oracle_lp_sum(const float* x, const float* q, int32_t d, double p) {
   return s;
 }
 
-/* Base metric: metric 1 -> L1 sum |d_j|; metric 2 -> squared L2 sum d_j^2. */
+/* Base metric: metric 1 -> L1 sum |d_j|; metric 2 -> squared L2 sum d_j^2;
+ * metric 3 -> L0.5 sum |d_j|^(1/2). */
 double oracle_base_dist(const float* x, const float* q, int32_t d, int32_t metric) {
   double s = 0.0;
   for (int32_t j = 0; j < d; ++j) {
     double diff = (double)x[j] - (double)q[j];
     if (metric == 1) s += fabs(diff);
+    else if (metric == 3) s += sqrt(fabs(diff));
     else s += diff * diff;
   }
   return s;
 }
+
+/* The p of a base metric, and whether the code is one. */
+static double metric_p(int32_t metric) {
+  return metric == 1 ? 1.0 : metric == 2 ? 2.0 : 0.5;
+}
+static int valid_metric(int32_t metric) { return metric == 1 || metric == 2 || metric == 3; }
 
 /* (da, ia) precedes (db, ib) in the (distance, id) order */
 static int pair_less(double da, int64_t ia, double db, int64_t ib) {
@@ -358,7 +370,7 @@ void oracle_graph_free(oracle_graph* g) {
 oracle_graph* oracle_hnsw_build(const float* base, int64_t n, int32_t d, int32_t metric, int32_t M,
                                 int32_t M0, int32_t efc, const int32_t* levels, int32_t* status) {
   *status = OR_EINVAL;
-  if (n <= 0 || d <= 0 || (metric != 1 && metric != 2) || M < 2 || M0 < M || efc < 1) return NULL;
+  if (n <= 0 || d <= 0 || !valid_metric(metric) || M < 2 || M0 < M || efc < 1) return NULL;
   oracle_graph* g = (oracle_graph*)calloc(1, sizeof(oracle_graph));
   if (!g) { *status = OR_ENOMEM; return NULL; }
   g->n = n; g->d = d; g->metric = metric; g->M = M; g->M0 = M0; g->efc = efc;
@@ -498,7 +510,7 @@ void oracle_graph_level_copy(const oracle_graph* g, int32_t l, int32_t* nodes, i
 int oracle_hnsw_search(const oracle_csr* g, const float* base, int32_t d, int32_t metric,
                        const float* q, int32_t ef, int32_t t, int64_t* out_ids, double* out_d,
                        int64_t* n_dist) {
-  if (ef < 1 || t < 1 || (metric != 1 && metric != 2)) return OR_EINVAL;
+  if (ef < 1 || t < 1 || !valid_metric(metric)) return OR_EINVAL;
   gview_t view = {NULL, NULL, g};
   visited_t vis = {(uint32_t*)calloc(g->n, sizeof(uint32_t)), 0, g->n};
   pset_t W = {0};
@@ -630,24 +642,29 @@ int oracle_verify_paper(const float* base, int32_t d, const float* q, double p, 
 /* ------------------------------------------------------------------ */
 
 /*
- * p == 1 or p == 2 (exactly, in FP32): direct K-NN on G1 or G2 with
- * ef' = max(ef, k); the returned distance is the base distance (L1, or the
- * square root of the squared L2 sum).
- * Otherwise: G1 if p <= cutoff (FP32 compare), else G2; C <- KnnSearch(q, t)
- * with t' = max(t or ef, k) and ef' = max(ef, t'); then verify C (mode 0:
- * exact with abandon; mode 1: Algorithm 1's batches).  The returned distance
- * is S^(1/p).  Counters: stats[0] = base-distance evaluations (N_b),
- * stats[1] = L_p candidates computed (N_p), stats[2] = L_p terms.
+ * Routing (Algorithm 1, lines 1-5), for graphs ga and gb under base metrics
+ * ma and mb (U-HNSW: L1 and L2; U-HNSW-E: L0.5 and L1): when p equals a
+ * graph's base p exactly (in FP32), direct K-NN on that graph with
+ * ef' = max(ef, k), and the returned distance is the base distance's root
+ * S^(1/p_base).  Otherwise ga if p <= cutoff (FP32 compare), else gb;
+ * C <- KnnSearch(q, t) with t' = max(t or ef, k) and ef' = max(ef, t'); then
+ * verify C (mode 0: exact with abandon; mode 1: Algorithm 1's batches).  The
+ * returned distance is S^(1/p).  Counters: stats[0] = base-distance
+ * evaluations (N_b), stats[1] = L_p candidates computed (N_p), stats[2] = L_p
+ * terms.
  */
-int oracle_uhnsw_query(const oracle_csr* g1, const oracle_csr* g2, const float* base, int32_t d,
-                       const float* q, float p, int32_t k, int32_t ef, int32_t t, float tau,
-                       int32_t kappa, float cutoff, int32_t mode, int64_t* out_ids,
-                       double* out_dist, int64_t* stats) {
+int oracle_uhnsw_query(const oracle_csr* ga, const oracle_csr* gb, int32_t ma, int32_t mb,
+                       const float* base, int32_t d, const float* q, float p, int32_t k,
+                       int32_t ef, int32_t t, float tau, int32_t kappa, float cutoff,
+                       int32_t mode, int64_t* out_ids, double* out_dist, int64_t* stats) {
   if (k < 1 || ef < 1 || !(p > 0.0f) || !(p <= 2.0f)) return OR_EINVAL;
+  if (!valid_metric(ma) || !valid_metric(mb)) return OR_EINVAL;
   int64_t nb = 0, np = 0, nterm = 0;
-  int direct = (p == 1.0f) || (p == 2.0f);
-  int32_t metric = direct ? (p == 1.0f ? 1 : 2) : (p <= cutoff ? 1 : 2);
-  const oracle_csr* g = metric == 1 ? g1 : g2;
+  const float pa = (float)metric_p(ma), pb = (float)metric_p(mb);
+  int use_a = (p == pa) ? 1 : (p == pb) ? 0 : (p <= cutoff);
+  int32_t metric = use_a ? ma : mb;
+  int direct = p == (float)metric_p(metric);
+  const oracle_csr* g = use_a ? ga : gb;
   int32_t tt = direct ? k : (t > 0 ? t : ef);
   if (tt < k) tt = k;
   int32_t efp = ef > tt ? ef : tt;
@@ -661,7 +678,8 @@ int oracle_uhnsw_query(const oracle_csr* g1, const oracle_csr* g2, const float* 
   if (direct) {
     for (int32_t j = 0; j < k; ++j) {
       out_ids[j] = C[j];
-      out_dist[j] = C[j] < 0 ? INFINITY : (metric == 1 ? Cd[j] : sqrt(Cd[j]));
+      out_dist[j] = C[j] < 0 ? INFINITY
+                             : metric == 1 ? Cd[j] : metric == 2 ? sqrt(Cd[j]) : Cd[j] * Cd[j];
     }
   } else {
     for (int32_t j = 0; j < tt; ++j) C32[j] = (int32_t)C[j];

@@ -12,6 +12,7 @@ Streams for a workload with seed ``s``:
   s+2   per-query p, k and ef
   s+3   HNSW levels of the L1 graph (G1)
   s+4   HNSW levels of the L2 graph (G2)
+  s+5   HNSW levels of the L0.5 graph (G0.5, U-HNSW-E)
 
 The HNSW level of each node is a random draw of the index construction
 (level = floor(-ln(U) * mL), mL = 1/ln(M), U uniform in (0, 1]); it is drawn
@@ -185,8 +186,8 @@ def hnsw_levels(n: int, M: int, seed: int) -> np.ndarray:
 
 
 def graph_levels(w: Workload, metric: int) -> np.ndarray:
-    """Levels for G1 (metric=1) or G2 (metric=2) of workload `w`."""
-    return hnsw_levels(w.n, w.M, w.seed + (3 if metric == 1 else 4))
+    """Levels for G1 (metric=1), G2 (metric=2) or G0.5 (metric=3) of workload `w`."""
+    return hnsw_levels(w.n, w.M, w.seed + {1: 3, 2: 4, 3: 5}[metric])
 
 
 def random_candidates(n: int, nq: int, t: int, seed: int, missing_frac: float = 0.0) -> np.ndarray:

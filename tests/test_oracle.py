@@ -360,3 +360,84 @@ def test_uhnsw_routing_cutoff(mixture_small):
 def test_recall_definition():
     assert oracle.recall([[1, 2, 3]], [[3, 4, 1]]) == pytest.approx(2 / 3)
     assert oracle.recall([[1, 2], [5, 6]], [[1, 2], [6, 7]]) == pytest.approx(0.75)
+
+
+# ----------------------------------------------------------------- U-HNSW-E (Section 4.6)
+def test_base_dist_l05_pins():
+    """Metric 3 is sum |d_j|^(1/2): a hand value, and scipy's Minkowski p = 0.5
+    distance, which is that sum squared."""
+    x = np.array([0.0, 4.0, 9.0, 2.5], np.float32)
+    q = np.array([1.0, 0.0, 0.0, 2.5], np.float32)
+    assert oracle.base_dist(x, q, 3) == 1.0 + 2.0 + 3.0 + 0.0
+    r = rng(11)
+    X = r.normal(size=(20, 24)).astype(np.float32)
+    Q = r.normal(size=(3, 24)).astype(np.float32)
+    D = cdist(Q.astype(np.float64), X.astype(np.float64), "minkowski", p=0.5)
+    for i in range(3):
+        got = [oracle.base_dist(X[j], Q[i], 3) for j in range(20)]
+        np.testing.assert_allclose(got, np.sqrt(D[i]), rtol=1e-12)
+
+
+@pytest.fixture(scope="module")
+def mixture_e():
+    w = I.WORKLOADS["mixture10k"].scaled(n=2000, nq=12)
+    base = I.base_vectors(w)
+    qs = I.query_vectors(w)
+    g05 = oracle.hnsw_build(base, 3, w.M, w.ef_construction, I.graph_levels(w, 3))
+    g1 = oracle.hnsw_build(base, 1, w.M, w.ef_construction, I.graph_levels(w, 1))
+    return w, base, qs, g05, g1
+
+
+def test_l05_graph_search_exact_at_full_beam(mixture_e):
+    """ef >= N on the L0.5 graph gives the exact L0.5 top-t (brute force by
+    scipy's Minkowski p = 0.5), and the graph keeps HNSW's degree caps."""
+    w, base, qs, g05, g1 = mixture_e
+    n = len(base)
+    assert max(np.diff(g05["levels"][0]["offsets"]).max(), 0) <= 2 * w.M
+    D = cdist(qs.astype(np.float64), base.astype(np.float64), "minkowski", p=0.5)
+    for i in range(4):
+        ids, dd, _ = oracle.hnsw_search(g05, base, qs[i], 3, n, 10)
+        order = np.lexsort((np.arange(n), D[i]))[:10]
+        np.testing.assert_array_equal(ids, order)
+        np.testing.assert_allclose(dd, np.sqrt(D[i, order]), rtol=1e-12)
+
+
+def test_uhnsw_e_direct_and_full_candidate_set(mixture_e):
+    """U-HNSW-E (G0.5 and G1, cutoff 0.6): p = 0.5 is direct K-NN on G0.5 and
+    p = 1 on G1, with no verification; with t = ef = N every p in [0.2, 1]
+    returns the exact L_p top-K (O1)."""
+    w, base, qs, g05, g1 = mixture_e
+    n = len(base)
+    E = dict(cutoff=0.6, metrics=(3, 1))
+    D05 = cdist(qs[:3].astype(np.float64), base.astype(np.float64), "minkowski", p=0.5)
+    D1 = cdist(qs[:3].astype(np.float64), base.astype(np.float64), "cityblock")
+    for pp, D in ((0.5, D05), (1.0, D1)):
+        ids, dist, st = oracle.uhnsw_batch(g05, g1, base, qs[:3], pp, 10, n, **E)
+        for i in range(3):
+            order = np.lexsort((np.arange(n), D[i]))[:10]
+            np.testing.assert_array_equal(ids[i], order)
+            np.testing.assert_allclose(dist[i], D[i, order], rtol=1e-12)
+        assert (st[:, 1] == 0).all()
+    pe = np.array([0.2, 0.3, 0.45, 0.6, 0.65, 0.8, 0.95, 0.55], np.float32)
+    ids_e, S_e = oracle.exact_knn(base, qs[:8], pe, 10)
+    ids, dist, _ = oracle.uhnsw_batch(g05, g1, base, qs[:8], pe, 10, n, t=n, tau=1.5, **E)
+    np.testing.assert_array_equal(ids, ids_e)
+    np.testing.assert_allclose(dist, S_e ** (1 / pe[:, None].astype(np.float64)), rtol=1e-12)
+
+
+def test_uhnsw_e_routing_cutoff(mixture_e):
+    """p <= 0.6 searches the first graph (G0.5), p > 0.6 the second (G1): a
+    second graph whose entry point has no links returns only that entry."""
+    w, base, qs, g05, g1 = mixture_e
+    n = len(base)
+    dead = {"num_levels": 1, "entry_point": 7, "max_degree0": 2, "max_degree": 2, "n": n,
+            "levels": [{"nodes": np.arange(n, dtype=np.int32),
+                        "offsets": np.zeros(n + 1, np.int64), "nbrs": np.zeros(0, np.int32)}]}
+    E = dict(cutoff=0.6, metrics=(3, 1))
+    lo, _, _ = oracle.uhnsw_query(g05, dead, base, qs[0], np.float32(0.6), 5, 32, **E)
+    hi, _, _ = oracle.uhnsw_query(g05, dead, base, qs[0],
+                                  np.nextafter(np.float32(0.6), np.float32(2)), 5, 32, **E)
+    one, _, _ = oracle.uhnsw_query(g05, dead, base, qs[0], np.float32(1.0), 5, 32, **E)
+    assert (lo >= 0).all()
+    assert hi.tolist() == [7, -1, -1, -1, -1]
+    assert one.tolist() == [7, -1, -1, -1, -1]     # p = 1 is the second graph's own metric
