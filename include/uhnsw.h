@@ -9,7 +9,9 @@
  * under the base metric form the candidate set C, which is re-ranked under
  * L_p ("Candidate verification", Algorithm 1 lines 6-10).  p == 1 and p == 2
  * search G1 / G2 for the K nearest directly, without verification (Section 3,
- * introduction).
+ * introduction).  In general a query whose p equals a graph's base p is
+ * answered directly on that graph; U-HNSW-E (Section 4.6) loads graphs under
+ * L0.5 and L1 (uhnsw_load_opts.base_metric) and routes with cutoff 0.6.
  *
  * Conventions for every entry point:
  *   - Return value: UHNSW_OK (0) or a negative UHNSW_E* code; nothing throws
@@ -81,11 +83,26 @@ typedef struct {
   const int32_t* level_nbrs[UHNSW_MAX_LEVELS];
 } uhnsw_graph;
 
+/* Base metric of a graph (the metric it was built under and is searched
+ * with).  UHNSW_BASE_L2 is the squared L2 sum and UHNSW_BASE_L05 the L0.5 sum
+ * without its root; each orders points exactly like its L_p metric. */
+typedef enum {
+  UHNSW_BASE_L1 = 1,   /* sum |d_j|,       p = 1   */
+  UHNSW_BASE_L2 = 2,   /* sum d_j^2,       p = 2   */
+  UHNSW_BASE_L05 = 3   /* sum |d_j|^(1/2), p = 0.5 */
+} uhnsw_base_metric;
+
 typedef struct {
   /* storage of the copy the beam search reads (the FP32 master copy is kept
    * for verification and returned distances either way) */
   uhnsw_dtype traverse_dtype;
-  int32_t reserved[7];
+  /* base metrics of the two graph slots; 0 => UHNSW_BASE_L1 for the first
+   * (g1) and UHNSW_BASE_L2 for the second (g2), which is U-HNSW.  U-HNSW-E
+   * (Section 4.6) loads a graph built under L0.5 as g1 and one built under
+   * L1 as g2 ({UHNSW_BASE_L05, UHNSW_BASE_L1}) and searches with cutoff 0.6.
+   * The first slot's base p must be below the second's. */
+  int32_t base_metric[2];
+  int32_t reserved[5];
 } uhnsw_load_opts;
 
 /* per-query counters written when uhnsw_search_opts.stats is set */
@@ -96,7 +113,7 @@ enum {
   UHNSW_STAT_EXPANSIONS = 3,/* beam entries expanded at layer 0 */
   UHNSW_STAT_RESETS = 4,    /* visited-table resets */
   UHNSW_STAT_STATUS = 5,    /* 0 or a negative UHNSW_E* code for this query */
-  UHNSW_STAT_GRAPH = 6,     /* 1 = G1 (L1), 2 = G2 (L2) */
+  UHNSW_STAT_GRAPH = 6,     /* graph slot searched: 1 = g1 (G1, L1), 2 = g2 (G2, L2) */
   UHNSW_STAT_ADJ = 7,       /* adjacency rows read (upper levels and layer 0) */
   UHNSW_NSTATS = 8
 };
@@ -106,7 +123,7 @@ typedef struct {
   int32_t kappa;         /* batch size of Algorithm 1; 0 => k */
   float tau;             /* early-termination threshold of Algorithm 1; 0 => 0.92;
                             a negative value stops after the first batch */
-  float cutoff;          /* routing: p <= cutoff searches G1; 0 => 1.4 */
+  float cutoff;          /* routing: p <= cutoff searches the first graph (G1); 0 => 1.4 */
   int32_t verify_mode;   /* uhnsw_verify_mode */
   int32_t search_width;  /* beam entries expanded per step; <= 1 => exactly HNSW's order */
   int32_t persistent;    /* 1: persistent launch pulling queries from a device queue.  The
@@ -136,7 +153,8 @@ typedef struct {
 } uhnsw_search_opts;
 
 /*
- * Upload an index: base vectors plus G1 (L1) and G2 (L2).
+ * Upload an index: base vectors plus two graphs, G1 (L1) and G2 (L2) unless
+ * opts->base_metric says otherwise.
  *   base      host, n x d float32 row-major; copied to an FP32 master copy and,
  *             if opts->traverse_dtype != UHNSW_F32, a rounded FP16/BF16 copy.
  *             Rows are zero-padded on the device to a multiple of 8 elements.
@@ -162,8 +180,8 @@ int uhnsw_load(const float* base, int64_t n, int32_t d, const uhnsw_graph* g1,
  *   out_dist   device, nq x k_max float32 (L_p distance S^(1/p))
  *   opts       may be NULL (defaults above)
  * The beam of a query holds ef' = max(ef, t', k) entries, t' = max(t or ef, k)
- * for general p, t' = k for p in {1, 2}.  For p in {1, 2} the first k beam
- * entries are returned directly when the beam ran on the FP32 rows or on an
+ * for general p, t' = k when p is a graph's base p.  For such a p the first k
+ * beam entries are returned directly when the beam ran on the FP32 rows or on an
  * FP16/BF16 copy that holds every value exactly (checked at load); with an
  * inexact copy the whole beam is re-ranked by its FP32 base distance, so
  * returned distances are always FP32 ones.  ef' above the launch bound
@@ -370,7 +388,8 @@ typedef struct uhnsw_built uhnsw_built;
 /*
  * Build one HNSW graph on the host.
  *   base      host n x d float32 row-major (read during the call only)
- *   metric    1 = L1 (G1), 2 = squared L2 (G2)
+ *   metric    a uhnsw_base_metric: 1 = L1 (G1), 2 = squared L2 (G2), 3 = L0.5
+ *             (G0.5 of U-HNSW-E)
  *   M         links per inserted node; layer-0 lists hold up to 2M
  *   ef_construction   beam width of the insertion search
  *   levels    host [n] int32, the level of each node (drawn by the caller)

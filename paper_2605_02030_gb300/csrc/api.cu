@@ -83,6 +83,7 @@ struct uhnsw_index {
   int32_t d = 0, d_pad = 0;
   uhnsw_dtype tdtype = UHNSW_F32;
   bool trav_exact = true;  // the traversal copy reproduces every FP32 value
+  int32_t gmetric[2] = {UHNSW_BASE_L1, UHNSW_BASE_L2};  // base metric of each graph slot
   float* base32 = nullptr;
   void* trav = nullptr;
   DevGraph g[2];
@@ -229,6 +230,9 @@ GraphDev to_dev(const DevGraph& g) {
 
 constexpr int kBlock = 128;
 
+// The p of a base metric (uhnsw_base_metric).
+double base_metric_p(int32_t m) { return m == UHNSW_BASE_L1 ? 1.0 : m == UHNSW_BASE_L2 ? 2.0 : 0.5; }
+
 }  // namespace
 
 extern "C" const char* uhnsw_last_error(void) { return uhnsw_internal::g_err; }
@@ -245,6 +249,16 @@ extern "C" int uhnsw_load(const float* base, int64_t n, int32_t d, const uhnsw_g
   const uhnsw_dtype dt = opts ? opts->traverse_dtype : UHNSW_F32;
   if (dt != UHNSW_F32 && dt != UHNSW_F16 && dt != UHNSW_BF16)
     return fail(UHNSW_EINVAL, "uhnsw_load: unknown traverse dtype %d", (int)dt);
+  int32_t gm[2] = {UHNSW_BASE_L1, UHNSW_BASE_L2};
+  for (int i = 0; i < 2; ++i) {
+    const int32_t m = opts ? opts->base_metric[i] : 0;
+    if (m == 0) continue;
+    if (m != UHNSW_BASE_L1 && m != UHNSW_BASE_L2 && m != UHNSW_BASE_L05)
+      return fail(UHNSW_EINVAL, "uhnsw_load: base_metric[%d]=%d is not a uhnsw_base_metric", i, m);
+    gm[i] = m;
+  }
+  if (!(base_metric_p(gm[0]) < base_metric_p(gm[1])))
+    return fail(UHNSW_EINVAL, "uhnsw_load: the first graph's base p must be below the second's");
 
   std::vector<int32_t> ell[2], upr[2], upa[2];
   try {
@@ -274,6 +288,8 @@ extern "C" int uhnsw_load(const float* base, int64_t n, int32_t d, const uhnsw_g
   idx->d = d;
   idx->d_pad = (d + 7) / 8 * 8;
   idx->tdtype = dt;
+  idx->gmetric[0] = gm[0];
+  idx->gmetric[1] = gm[1];
   int rc = UHNSW_OK;
   const size_t row32 = (size_t)idx->d_pad * 4;
   do {
@@ -442,6 +458,10 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   a.d_pad = idx->d_pad;
   a.g[0] = to_dev(idx->g[0]);
   a.g[1] = to_dev(idx->g[1]);
+  for (int i = 0; i < 2; ++i) {
+    a.gmetric[i] = idx->gmetric[i];
+    a.gp[i] = (float)base_metric_p(idx->gmetric[i]);
+  }
   a.q = q;
   a.p = p;
   a.k = k;

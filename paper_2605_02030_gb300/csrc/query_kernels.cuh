@@ -55,7 +55,9 @@ struct QueryArgs {
   const void* trav;     // traversal copy [n][d_pad] in the kernel's element type
   int64_t n;
   int32_t d, d_pad;
-  GraphDev g[2];        // G1 (L1), G2 (squared L2)
+  GraphDev g[2];        // graph slots: G1 (L1) and G2 (squared L2), or G0.5 and G1
+  int32_t gmetric[2];   // base metric of each slot (uhnsw_base_metric)
+  float gp[2];          // the p of each slot's base metric
   const float* q;       // [nq][d]
   const float* p;       // [nq]
   const int32_t* k;     // [nq] or null (k_max)
@@ -86,6 +88,26 @@ struct QueryArgs {
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
+
+// Routing of a query (Algorithm 1, lines 1-5): the graph slot it searches,
+// whether it is answered directly (p is that graph's own base p), and the
+// slot's base metric.  p <= cutoff selects the first slot.
+struct Route {
+  int slot;
+  bool direct;
+  int metric;
+};
+__device__ __forceinline__ Route route_query(const QueryArgs& a, float p) {
+  const int slot = p == a.gp[0] ? 0 : p == a.gp[1] ? 1 : (p <= a.cutoff ? 0 : 1);
+  return Route{slot, p == a.gp[slot], a.gmetric[slot]};
+}
+
+// The distance a direct query returns: the base sum's root S^(1/p_base).
+__device__ __forceinline__ float base_root(int metric, float s) {
+  return metric == UHNSW_BASE_L1 ? s
+         : metric == UHNSW_BASE_L2 ? sqrtf(s)
+                                   : (float)((double)s * (double)s);
+}
 
 // Dynamic shared-memory carve-up (byte offsets), identical on host and device.
 struct SmemLayout {
@@ -213,7 +235,8 @@ __device__ __forceinline__ void dist_batch(const T* __restrict__ rows, int d_pad
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
           const float df = x[e] - qv[c][e];
-          if (METRIC == 1) acc += fabsf(df);
+          if (METRIC == UHNSW_BASE_L1) acc += fabsf(df);
+          else if (METRIC == UHNSW_BASE_L05) acc += hw_sqrt(fabsf(df));
           else acc = fmaf(df, df, acc);
         }
       }
@@ -230,8 +253,9 @@ __device__ __forceinline__ void dist_batch_metric(int metric, const T* rows, int
                                                   const float (&qv)[CPL][Elems16<T>::n],
                                                   const uint32_t* ids, float* out, int m,
                                                   int64_t n, int32_t* err) {
-  if (metric == 1) dist_batch<T, TEAM, CPL, BLOCK, 1>(rows, d_pad, qv, ids, out, m, n, err);
-  else dist_batch<T, TEAM, CPL, BLOCK, 2>(rows, d_pad, qv, ids, out, m, n, err);
+  if (metric == UHNSW_BASE_L1) dist_batch<T, TEAM, CPL, BLOCK, 1>(rows, d_pad, qv, ids, out, m, n, err);
+  else if (metric == UHNSW_BASE_L2) dist_batch<T, TEAM, CPL, BLOCK, 2>(rows, d_pad, qv, ids, out, m, n, err);
+  else dist_batch<T, TEAM, CPL, BLOCK, 3>(rows, d_pad, qv, ids, out, m, n, err);
 }
 
 // ---------------------------------------------------------------- verification
@@ -475,12 +499,13 @@ __device__ void run_query(const QueryArgs& a, int64_t qi, unsigned char* smem, c
   const float p = a.p[qi];
   const int k = a.k ? a.k[qi] : a.k_max;
   const int ef = a.ef ? a.ef[qi] : a.ef_default;
-  const bool direct = (p == 1.0f) || (p == 2.0f);
-  const int metric = direct ? (p == 1.0f ? 1 : 2) : (p <= a.cutoff ? 1 : 2);
+  const Route rt = route_query(a, p);
+  const bool direct = rt.direct;
+  const int metric = rt.metric;
   int tt = direct ? k : (a.t > 0 ? a.t : ef);
   if (tt < k) tt = k;
   const int efp = max(ef, tt);
-  const GraphDev& g = a.g[metric - 1];
+  const GraphDev& g = a.g[rt.slot];
   const bool ok = (p > 0.f) && (p <= 2.f) && k >= 1 && k <= a.k_max && ef >= 1 &&
                   efp <= a.ef_cap && g.ell0 != nullptr && a.width * g.deg0 <= a.cmax &&
                   g.deg <= a.cmax;
@@ -641,13 +666,13 @@ __device__ void run_query(const QueryArgs& a, int64_t qi, unsigned char* smem, c
       if (j < k && j < bn) {
         oid[j] = (int64_t)(bi[cb][j] & kIdMask);
         const float dd = bd[cb][j];
-        odist[j] = metric == 1 ? dd : sqrtf(dd);
+        odist[j] = base_root(metric, dd);
       } else {
         oid[j] = -1;
         odist[j] = __int_as_float(0x7f800000);
       }
     }
-    write_stats(a, qi, nb, 0, 0, nexp, nres, 0, metric, nadj);
+    write_stats(a, qi, nb, 0, 0, nexp, nres, 0, rt.slot + 1, nadj);
     return;
   }
   VerifyBufs vb;
@@ -663,7 +688,7 @@ __device__ void run_query(const QueryArgs& a, int64_t qi, unsigned char* smem, c
   const int kappa = a.kappa > 0 ? a.kappa : k;
   verify_dispatch<BLOCK>(a, qs, p, bi[cb], nc, k, kappa, direct, vb, s, vc);
   write_verified<BLOCK>(a, qi, p, k, vb, s, vc);
-  write_stats(a, qi, nb, s.np, s.terms, nexp, nres, 0, metric, nadj);
+  write_stats(a, qi, nb, s.np, s.terms, nexp, nres, 0, rt.slot + 1, nadj);
 }
 
 template <typename T, int TEAM, int CPL, int BLOCK>

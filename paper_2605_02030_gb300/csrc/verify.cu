@@ -69,8 +69,7 @@ bool pick_shape(uhnsw_dtype dt, int chunks, TeamShape* out) {
 }
 
 // Beam ef' of a query exactly as the search kernels derive it.
-__device__ __forceinline__ int query_beam(float p, int k, int ef, int t) {
-  const bool direct = (p == 1.0f) || (p == 2.0f);
+__device__ __forceinline__ int query_beam(bool direct, int k, int ef, int t) {
   int tt = direct ? k : (t > 0 ? t : ef);
   if (tt < k) tt = k;
   return max(ef, tt);
@@ -82,38 +81,41 @@ __device__ __forceinline__ int beam_bucket(const BeamBuckets& bb, int efp) {
   return bb.n - 1;  // beyond every bound: the query fails validation there
 }
 
-// Code route of a query: graph (L1 / L2) and the p form of its verification
-// (none for the direct p = 1 / 2, then p = 0.5, p = 1.5, general p).  Queries
-// of one route run the same instructions, so grouping them keeps the code
-// that the warps of an SM execute at the same time small.
-__device__ __forceinline__ int query_route(float p, float cutoff) {
-  const bool direct = (p == 1.0f) || (p == 2.0f);
-  const int metric = direct ? (p == 1.0f ? 0 : 1) : (p <= cutoff ? 0 : 1);
+// Code route of a query: graph slot (with the same rule as the search
+// kernels' route_query) and the p form of its verification (none for a
+// direct query, then p = 0.5, p = 1.5, general p).  Queries of one route run
+// the same instructions, so grouping them keeps the code that the warps of an
+// SM execute at the same time small.
+__device__ __forceinline__ int query_route(float p, float cutoff, float gp0, float gp1) {
+  const int slot = p == gp0 ? 0 : p == gp1 ? 1 : (p <= cutoff ? 0 : 1);
+  const bool direct = p == (slot == 0 ? gp0 : gp1);
   const int form = direct ? 0 : p == 0.5f ? 1 : p == 1.5f ? 2 : 3;
-  return metric * 4 + form;
+  return slot * 4 + form;
 }
 
 __device__ __forceinline__ int query_bin(const BeamBuckets& bb, const float* p, const int32_t* k,
                                          const int32_t* ef, int64_t i, int k_max, int ef_default,
-                                         int t, float cutoff) {
-  const int b = beam_bucket(bb, query_beam(p[i], k ? k[i] : k_max, ef ? ef[i] : ef_default, t));
-  return b * kRoutes + query_route(p[i], cutoff);
+                                         int t, float cutoff, float gp0, float gp1) {
+  const bool direct = p[i] == gp0 || p[i] == gp1;
+  const int b = beam_bucket(bb, query_beam(direct, k ? k[i] : k_max, ef ? ef[i] : ef_default, t));
+  return b * kRoutes + query_route(p[i], cutoff, gp0, gp1);
 }
 
 // Counting sort of the query indices by (beam bucket, route): counts, then
 // slots.  ws[0..64): counts per bin, ws[64..128): cursors; info[2b] = first
 // slot of bucket b, info[2b+1] = its count.
 __global__ void bucket_count_kernel(const float* p, const int32_t* k, const int32_t* ef, int64_t nq,
-                                    int k_max, int ef_default, int t, float cutoff,
-                                    BeamBuckets bb, int32_t* ws) {
+                                    int k_max, int ef_default, int t, float cutoff, float gp0,
+                                    float gp1, BeamBuckets bb, int32_t* ws) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq;
        i += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&ws[query_bin(bb, p, k, ef, i, k_max, ef_default, t, cutoff)], 1);
+    atomicAdd(&ws[query_bin(bb, p, k, ef, i, k_max, ef_default, t, cutoff, gp0, gp1)], 1);
 }
 
 __global__ void bucket_scatter_kernel(const float* p, const int32_t* k, const int32_t* ef,
                                       int64_t nq, int k_max, int ef_default, int t, float cutoff,
-                                      BeamBuckets bb, int32_t* ws, int32_t* order, int32_t* info) {
+                                      float gp0, float gp1, BeamBuckets bb, int32_t* ws,
+                                      int32_t* order, int32_t* info) {
   if (blockIdx.x == 0 && threadIdx.x < bb.n) {
     const int b = threadIdx.x;
     int first = 0, cnt = 0;
@@ -124,7 +126,7 @@ __global__ void bucket_scatter_kernel(const float* p, const int32_t* k, const in
   }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int bin = query_bin(bb, p, k, ef, i, k_max, ef_default, t, cutoff);
+    const int bin = query_bin(bb, p, k, ef, i, k_max, ef_default, t, cutoff, gp0, gp1);
     int base = 0;
     for (int j = 0; j < bin; ++j) base += ws[j];
     const int pos = atomicAdd(&ws[kBins + bin], 1);
@@ -139,12 +141,13 @@ cudaError_t launch_bucketing(const QueryArgs& a, const BeamBuckets& bb, int32_t*
   int64_t blocks = (a.nq + 255) / 256;
   if (blocks > 1024) blocks = 1024;
   bucket_count_kernel<<<(unsigned)blocks, 256, 0, st>>>(a.p, a.k, a.ef, a.nq, a.k_max,
-                                                         a.ef_default, a.t, a.cutoff, bb, ws);
+                                                         a.ef_default, a.t, a.cutoff, a.gp[0],
+                                                         a.gp[1], bb, ws);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   bucket_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(a.p, a.k, a.ef, a.nq, a.k_max,
-                                                           a.ef_default, a.t, a.cutoff, bb, ws,
-                                                           order, info);
+                                                           a.ef_default, a.t, a.cutoff, a.gp[0],
+                                                           a.gp[1], bb, ws, order, info);
   return cudaGetLastError();
 }
 

@@ -116,7 +116,8 @@ __device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
   return r;
 }
 
-// Elementwise |x - q| summed (metric 1) or (x - q)^2 summed (metric 2) over
+// Elementwise |x - q| (metric 1), (x - q)^2 (metric 2) or |x - q|^(1/2)
+// (metric 3) summed over
 // one 16-byte chunk of a row, as even / odd element pairs accumulated into acc.
 // q holds the chunk's query values as FP32 pairs (little-endian: element 2e in
 // the low half).
@@ -129,8 +130,15 @@ __device__ __forceinline__ void chunk_partial(const uint4& v, const uint64_t (&q
 #pragma unroll
   for (int e = 0; e < VEC / 2; ++e) {
     const uint64_t df = f2_sub(f2_pack(x[2 * e], x[2 * e + 1]), q[e]);
-    if (METRIC == 1) acc = f2_add(acc, df & 0x7fffffff7fffffffull);
-    else acc = f2_fma(df, df, acc);
+    if (METRIC == UHNSW_BASE_L1) {
+      acc = f2_add(acc, df & 0x7fffffff7fffffffull);
+    } else if (METRIC == UHNSW_BASE_L05) {
+      float lo, hi;
+      asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(df));
+      acc = f2_add(acc, f2_pack(hw_sqrt(fabsf(lo)), hw_sqrt(fabsf(hi))));
+    } else {
+      acc = f2_fma(df, df, acc);
+    }
   }
 }
 
@@ -247,8 +255,9 @@ template <typename T, int TEAM, int CPL, int U>
 __device__ __forceinline__ void warp_dist_metric(int metric, const T* rows, int d_pad,
                                                  const float* qs, const uint32_t* ids, float* out,
                                                  int m, int64_t n, int32_t* err) {
-  if (metric == 1) warp_dist<T, TEAM, CPL, U, 1>(rows, d_pad, qs, ids, out, m, n, err);
-  else warp_dist<T, TEAM, CPL, U, 2>(rows, d_pad, qs, ids, out, m, n, err);
+  if (metric == UHNSW_BASE_L1) warp_dist<T, TEAM, CPL, U, 1>(rows, d_pad, qs, ids, out, m, n, err);
+  else if (metric == UHNSW_BASE_L2) warp_dist<T, TEAM, CPL, U, 2>(rows, d_pad, qs, ids, out, m, n, err);
+  else warp_dist<T, TEAM, CPL, U, 3>(rows, d_pad, qs, ids, out, m, n, err);
 }
 
 // Drops the candidates that cannot enter a full W (those not before its last
@@ -455,12 +464,13 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
   const float p = a.p[qi];
   const int k = a.k ? a.k[qi] : a.k_max;
   const int ef = a.ef ? a.ef[qi] : a.ef_default;
-  const bool direct = (p == 1.0f) || (p == 2.0f);
-  const int metric = direct ? (p == 1.0f ? 1 : 2) : (p <= a.cutoff ? 1 : 2);
+  const Route rt = route_query(a, p);
+  const bool direct = rt.direct;
+  const int metric = rt.metric;
   int tt = direct ? k : (a.t > 0 ? a.t : ef);
   if (tt < k) tt = k;
   const int efp = max(ef, tt);
-  const GraphDev g = metric == 1 ? a.g[0] : a.g[1];
+  const GraphDev g = rt.slot == 0 ? a.g[0] : a.g[1];
   const bool ok = (p > 0.f) && (p <= 2.f) && k >= 1 && k <= a.k_max && ef >= 1 &&
                   efp <= a.ef_cap && g.ell0 != nullptr && a.width * g.deg0 <= a.cmax &&
                   g.deg <= a.cmax;
@@ -639,13 +649,13 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
       if (j < k && j < bn) {
         oid[j] = (int64_t)(bic[j] & kIdMask);
         const float dd = bdc[j];
-        odist[j] = metric == 1 ? dd : sqrtf(dd);
+        odist[j] = base_root(metric, dd);
       } else {
         oid[j] = -1;
         odist[j] = kInf;
       }
     }
-    if (lane == 0) put_stats(a, qi, nb, 0, 0, nexp, nres, 0, metric, nadj);
+    if (lane == 0) put_stats(a, qi, nb, 0, 0, nexp, nres, 0, rt.slot + 1, nadj);
     return;
   }
   WarpVerify v;
@@ -669,7 +679,7 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
       odist[j] = kInf;
     }
   }
-  if (lane == 0) put_stats(a, qi, nb, v.np, v.terms, nexp, nres, 0, metric, nadj);
+  if (lane == 0) put_stats(a, qi, nb, v.np, v.terms, nexp, nres, 0, rt.slot + 1, nadj);
 }
 
 // WARPS independent queries per block; a.queue_head set = persistent (each

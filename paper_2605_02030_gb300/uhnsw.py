@@ -44,7 +44,14 @@ class _Graph(C.Structure):
 
 
 class _LoadOpts(C.Structure):
-    _fields_ = [("traverse_dtype", C.c_int32), ("reserved", C.c_int32 * 7)]
+    _fields_ = [("traverse_dtype", C.c_int32), ("base_metric", C.c_int32 * 2),
+                ("reserved", C.c_int32 * 5)]
+
+
+# Base metrics (uhnsw_base_metric): 1 = L1, 2 = squared L2, 3 = L0.5 sum.
+BASE_L1, BASE_L2, BASE_L05 = 1, 2, 3
+U_HNSW = (BASE_L1, BASE_L2)        # G1 and G2, cutoff 1.4
+U_HNSW_E = (BASE_L05, BASE_L1)     # G0.5 and G1, cutoff 0.6 (Section 4.6)
 
 
 class _SearchOpts(C.Structure):
@@ -160,7 +167,8 @@ def _stream_ptr(stream) -> C.c_void_p:
 # ----------------------------------------------------------------- graph building
 def build_graph(base: np.ndarray, metric: int, M: int, ef_construction: int, levels: np.ndarray,
                 threads: int = 0) -> dict:
-    """HNSW graph under L1 (metric=1) or squared L2 (metric=2), built on the host
+    """HNSW graph under L1 (metric=1), squared L2 (metric=2) or the L0.5 sum
+    (metric=3, U-HNSW-E's G0.5), built on the host
     by the library's multi-threaded insertion; returned as a CSR dict
     {num_levels, entry_point, max_degree0, max_degree, n, levels: [{nodes,
     offsets, nbrs}]} with level 0 listing every node."""
@@ -223,10 +231,12 @@ def _graph_struct(g: dict | None):
 
 # ----------------------------------------------------------------- index
 class Index:
-    """A loaded U-HNSW index (base vectors + G1 + G2) on the current CUDA device."""
+    """A loaded U-HNSW index (base vectors + two graphs) on the current CUDA
+    device.  metrics: base metrics of g1 and g2, U_HNSW (G1, G2) by default or
+    U_HNSW_E (G0.5, G1; search with cutoff=0.6)."""
 
     def __init__(self, base: np.ndarray, g1: dict | None, g2: dict | None,
-                 traverse_dtype: str = "f32"):
+                 traverse_dtype: str = "f32", metrics=U_HNSW):
         lib = load_library()
         base = np.ascontiguousarray(base, np.float32)
         self.n, self.d = base.shape
@@ -235,6 +245,8 @@ class Index:
         s2, k2 = _graph_struct(g2)
         opts = _LoadOpts()
         opts.traverse_dtype = DTYPES[traverse_dtype]
+        opts.base_metric[0], opts.base_metric[1] = int(metrics[0]), int(metrics[1])
+        self.metrics = tuple(metrics)
         h = C.c_void_p(0)
         _check(lib.uhnsw_load(_np_ptr(base), self.n, self.d,
                               C.byref(s1) if s1 is not None else None,

@@ -78,7 +78,8 @@ def test_build_graph_validation(lib):
     base = np.zeros((10, 4), np.float32)
     lv = np.zeros(10, np.int32)
     h = C.c_void_p(0)
-    assert lib.uhnsw_build_graph(base.ctypes.data, 10, 4, 3, 4, 10, lv.ctypes.data, 1, C.byref(h)) == -1
+    assert lib.uhnsw_build_graph(base.ctypes.data, 10, 4, 4, 4, 10, lv.ctypes.data, 1, C.byref(h)) == -1
+    assert lib.uhnsw_build_graph(base.ctypes.data, 10, 4, 0, 4, 10, lv.ctypes.data, 1, C.byref(h)) == -1
     assert lib.uhnsw_build_graph(base.ctypes.data, 10, 4, 1, 1, 10, lv.ctypes.data, 1, C.byref(h)) == -1
     lv[3] = -2
     assert lib.uhnsw_build_graph(base.ctypes.data, 10, 4, 1, 4, 10, lv.ctypes.data, 1, C.byref(h)) == -1
@@ -106,6 +107,18 @@ def test_builder_single_thread_equals_oracle(lib, case):
         go = oracle.hnsw_build(base, metric, w.M, w.ef_construction, lv)
         gp = U.build_graph(base, metric, w.M, w.ef_construction, lv, threads=1)
         assert _same_graph(go, gp), (name, metric)
+
+
+def test_builder_l05_single_thread_equals_oracle(lib):
+    """The L0.5 graph of U-HNSW-E (metric 3) on 0/1 data, where every |d_j|^(1/2)
+    is 0 or 1 and the FP32 sums are exact: one-thread insertion reproduces the
+    oracle's FP64 construction exactly."""
+    r = np.random.default_rng(13)
+    base = r.integers(0, 2, size=(1500, 32)).astype(np.float32)
+    lv = I.hnsw_levels(len(base), 8, 5)
+    go = oracle.hnsw_build(base, 3, 8, 30, lv)
+    gp = U.build_graph(base, 3, 8, 30, lv, threads=1)
+    assert _same_graph(go, gp)
 
 
 def test_builder_parallel_invariants(lib):
