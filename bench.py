@@ -102,11 +102,12 @@ def load_graph(path):
 
 
 def graphs_for(w: I.Workload, base: np.ndarray, log):
-    """G1 (L1) and G2 (L2) built by the library's multi-threaded HNSW insertion
+    """The workload's two graphs (G1 under L1 and G2 under L2, or G0.5 and G1
+    for U-HNSW-E) built by the library's multi-threaded HNSW insertion
     (Section 2.2), cached on disk keyed by the workload recipe."""
     os.makedirs(CACHE, exist_ok=True)
     out = []
-    for metric in (1, 2):
+    for metric in w.metrics:
         path = os.path.join(CACHE, f"graph_{w.name}_{_key(w.n, w.d, w.seed, w.M, w.ef_construction, metric)}.npz")
         if os.path.exists(path):
             out.append(load_graph(path))
@@ -114,7 +115,7 @@ def graphs_for(w: I.Workload, base: np.ndarray, log):
         from paper_2605_02030_gb300 import uhnsw as U
         t0 = time.time()
         g = U.build_graph(base, metric, w.M, w.ef_construction, I.graph_levels(w, metric), threads=0)
-        log(f"built G{metric} in {time.time() - t0:.1f} s")
+        log(f"built the metric-{metric} graph in {time.time() - t0:.1f} s")
         save_graph(path, g)
         out.append(g)
     return out
@@ -456,8 +457,9 @@ def _launches_per_call(ef_cap):
     return 2 + len([b for b in (64, 128, 256, 512) if b < ef_cap]) + 1
 
 
-def _p_bins(p):
-    return np.clip(np.floor((p - 0.5) / 0.1 + 1e-6).astype(int), 0, 15)
+def _p_bins(p, lo=0.5):
+    """Bins of width 0.1 starting at lo (the workload's lowest p)."""
+    return np.clip(np.floor((p - lo) / 0.1 + 1e-6).astype(int), 0, 15)
 
 
 def run_workload(args, log):
@@ -482,13 +484,13 @@ def run_workload(args, log):
     p, kq, efq = I.query_params(w)
     log(f"inputs {w.n}x{w.d}, {w.nq} queries in {time.time() - t0:.1f} s")
     g1, g2 = graphs_for(w, base, log)
-    idx = U.Index(base, g1, g2, traverse_dtype=w.traverse_dtype)
+    idx = U.Index(base, g1, g2, traverse_dtype=w.traverse_dtype, metrics=w.metrics)
     q_dev = torch.from_numpy(qs).cuda()
     p_dev = torch.from_numpy(p).cuda()
     stream = torch.cuda.Stream()
     k_max = int(kq.max())
     gt = ground_truth(w, idx, q_dev, p_dev, k_max, log)
-    bins = _p_bins(p)
+    bins = _p_bins(p, w.p_lo)
     flush = torch.empty(384 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     sample = np.random.default_rng(5).choice(w.nq, size=min(200, w.nq), replace=False)
     row_bytes = w.d * (2 if w.traverse_dtype in ("f16", "bf16") else 4)
@@ -587,12 +589,13 @@ def run_workload(args, log):
         idx.close()
         return
 
-    # unit10m: calibrate ef for recall@10 >= 0.95 in every p bin, then time the
-    # batched form and replay Poisson arrivals through the serving loop
+    # unit10m / sift1m_e: calibrate ef for recall@10 >= 0.95 in every p bin,
+    # then time the batched form (and, for unit10m, replay Poisson arrivals
+    # through the serving loop)
     k10 = np.full(w.nq, 10, np.int32)
     ef_op = None
     for ef in EF_SWEEP:
-        ids, _, _ = idx.search(q_dev, p_dev, k=10, ef=ef, persistent=True)
+        ids, _, _ = idx.search(q_dev, p_dev, k=10, ef=ef, persistent=True, cutoff=w.cutoff)
         torch.cuda.synchronize()
         hits = _recall_at_k(ids.cpu().numpy(), gt, k10)
         per = [float(hits[bins == b].mean()) for b in np.unique(bins)]
@@ -607,14 +610,44 @@ def run_workload(args, log):
            torch.empty((w.nq, k_max), dtype=torch.float32, device="cuda"))
     call = lambda ev: idx.search(q_dev, p_dev, k=k_dev, ef=ef_dev, k_max=k_max,
                                  ef_max=int(efk.max()), persistent=True, use_graph=True,
-                                 stream=stream, out=out, kernel_events=ev)
+                                 stream=stream, out=out, kernel_events=ev, cutoff=w.cutoff)
     with ClockSampler(torch.cuda.current_device()) as clk:
         ms, kern_ms = timed(call, args.steps)
     ids, dist = out[0].cpu().numpy(), out[1].cpu().numpy()
     _, _, st = idx.search(q_dev, p_dev, k=k_dev, ef=ef_dev, k_max=k_max, ef_max=int(efk.max()),
-                          stats=True)
+                          stats=True, cutoff=w.cutoff)
     st = st.cpu().numpy().astype(np.int64)
     hits_k = _recall_at_k(ids, gt, kq)
+    if args.workload == "sift1m_e":
+        hk = _recall_at_k(ids, gt, kq)
+        value = aggregate_value(args.steps * w.nq, 1, sum(ms) / 1e3)
+        line = {
+            "metric": "U-HNSW-E: QPS at recall@10>=0.95, p in (0.2,0.7], 1M\u00d7128, "
+                      "G0.5 + G1, cutoff 0.6", "value": round(value, 1), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(statistics.mean(ms), 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"sift1m_e: sift1m's N={w.n:,} d={w.d} base and {w.nq:,} "
+                                   f"queries, p ~ U({w.p_lo},{w.p_hi}], k=10; G0.5/G1 "
+                                   f"M={w.M} efConstruction={w.ef_construction}",
+                       "form": "FP16 traversal rows, FP32 verification, persistent launch, "
+                               "CUDA-graph replay",
+                       "ef": ef_op, "recall_at_10": round(rec10, 4),
+                       "recall_at_10_min_p_bin": round(rec10_min, 4),
+                       "recall_at_10_per_p_bin": {
+                           f"{w.p_lo + 0.1 * b:.1f}": round(float(hk[bins == b].mean()), 4)
+                           for b in np.unique(bins)},
+                       "dist_rel_err_vs_fp64_max": _dist_rel_err(base, qs, p, ids, dist, sample),
+                       "l2": "flushed (384 MB write) between timed steps",
+                       "stats_per_query": {"N_b": float(st[:, 0].mean()),
+                                           "N_p": float(st[:, 1].mean())}},
+            "roofline": roofline(st, kern_ms),
+            "clocks": clk.summary(),
+            "gpu_launches": args.steps * _launches_per_call(int(efk.max())),
+        }
+        print(json.dumps(line), flush=True)
+        idx.close()
+        return
     serving = []
     for rate in (5_000, 50_000, 100_000, 200_000):
         arr = np.cumsum(np.random.default_rng(7).exponential(1e6 / rate, size=w.nq))
@@ -744,9 +777,10 @@ def main():
                     help="comma-separated subset of the forms to run (the JSON line needs fp16_batched)")
     ap.add_argument("--query-threads", type=int, default=32, choices=(32, 128),
                     help="32: warp-per-query kernel, 128: block-per-query kernel")
-    ap.add_argument("--workload", default="sift1m", choices=("sift1m", "gist1m", "unit10m"),
+    ap.add_argument("--workload", default="sift1m",
+                    choices=("sift1m", "gist1m", "unit10m", "sift1m_e"),
                     help="sift1m: the headline line; gist1m: the batched form on 1M x 960 BF16; "
-                         "unit10m: the serving form on 10M x 96 FP16")
+                         "unit10m: the serving form on 10M x 96 FP16; sift1m_e: U-HNSW-E")
     ap.add_argument("--quiet", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

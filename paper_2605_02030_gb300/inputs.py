@@ -36,6 +36,9 @@ dataset item is reproduced):
                {32, 64, 128, 256, 512} with ef >= k; BF16 traversal copy.
   unit10m      N=10,000,000 d=96 N(0, I) rows scaled to unit L2 norm, FP16;
                p ~ U(0.5, 2]; k in {10, 50}.
+  sift1m_e     sift1m's base and queries for U-HNSW-E (Section 4.6): graphs
+               under L0.5 and L1, cutoff 0.6, p ~ U(0.2, 0.7] (the shifted
+               range of the paper's comparison); FP16 traversal copy.
 """
 from __future__ import annotations
 
@@ -63,6 +66,10 @@ class Workload:
     ef_construction: int = 100
     n_clusters: int = 16
     traverse_dtype: str = "f32"
+    p_lo: float = 0.5       # "uniform" p is drawn on (p_lo, p_hi]
+    p_hi: float = 2.0
+    metrics: tuple = (1, 2)  # base metrics of the two graphs (3 = L0.5)
+    cutoff: float = 1.4
     seed: int = 0
     grid: float = 0.0       # >0: round base and queries to multiples of `grid`
     extra: dict = field(default_factory=dict)
@@ -87,6 +94,9 @@ WORKLOADS = {
     "unit10m": Workload("unit10m", 10_000_000, 96, 10_000, "unit", "uniform", k=10,
                         k_choices=(10, 50), ef=128, M=32, ef_construction=200,
                         traverse_dtype="f16"),
+    "sift1m_e": Workload("sift1m_e", 1_000_000, 128, 10_000, "sift", "uniform", k=10, ef=64,
+                         M=32, ef_construction=200, n_clusters=1000, traverse_dtype="f16",
+                         p_lo=0.2, p_hi=0.7, metrics=(3, 1), cutoff=0.6),
 }
 
 
@@ -163,8 +173,8 @@ def query_params(w: Workload):
     if w.p_mode == "grid":
         p = P_GRID[rng.integers(0, len(P_GRID), size=w.nq)]
     else:
-        # uniform on (0.5, 2]: 2 - 1.5*U with U uniform on [0, 1)
-        p = (2.0 - 1.5 * rng.random(w.nq)).astype(np.float32)
+        # uniform on (p_lo, p_hi]: p_hi - (p_hi - p_lo) U with U uniform on [0, 1)
+        p = (w.p_hi - (w.p_hi - w.p_lo) * rng.random(w.nq)).astype(np.float32)
     if w.k_choices:
         k = np.asarray(w.k_choices, dtype=np.int32)[rng.integers(0, len(w.k_choices), size=w.nq)]
     else:
