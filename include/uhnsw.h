@@ -150,6 +150,13 @@ typedef struct {
                             launch and right after the last one: the search kernels' own
                             duration, without the queue-ordering kernels of a persistent
                             launch.  Such a call runs without CUDA-graph replay. */
+  const int32_t* t_per_query;  /* device [nq] or NULL: query i verifies t_i candidates in
+                                  place of t (0 => ef); ef' grows with t_i as above, so a
+                                  batch with per-query t needs ef_max (0 => 512).  The knob
+                                  of the t / tau trade-off (Section 3.2); uhnsw_plan_t
+                                  derives t per p from idealized recall. */
+  const float* tau_per_query;  /* device [nq] or NULL: query i's tau in place of tau (0 =>
+                                  0.92, negative => stop after the first batch) */
 } uhnsw_search_opts;
 
 /*
@@ -195,8 +202,9 @@ int uhnsw_search(uhnsw_index* idx, const float* q, const float* p, const int32_t
                  void* stream);
 
 /*
- * uhnsw_search with HOST arrays: q (nq x d), p, k, ef (or NULL) and the outputs
- * are host memory (pinned memory makes the copies asynchronous).  The call
+ * uhnsw_search with HOST arrays: q (nq x d), p, k, ef (or NULL), the outputs
+ * and opts->t_per_query / tau_per_query (if set) are host memory (pinned
+ * memory makes the copies asynchronous).  The call
  * copies the inputs to device staging buffers owned by the index, runs the
  * search on `stream` and copies the results back; it returns after the
  * stream has synchronised.  Not safe to run concurrently on one index.
@@ -233,6 +241,35 @@ int uhnsw_verify(uhnsw_index* idx, const float* q, const float* p, const int32_t
  */
 int uhnsw_exact(uhnsw_index* idx, const float* q, const float* p, int64_t nq, int32_t k,
                 int64_t* out_ids, float* out_dist, void* stream);
+
+/*
+ * Idealized recall of candidate sets (Section 3.2; the experiment the paper
+ * uses to choose t).  For each query, counts[i][t-1] = |T_K ∩ B_t| for
+ * t = 1 .. t_max, where T_K is the exact top-K under the query's own L_p and
+ * B_t the exact top-t under the base metric of the graph the query is routed
+ * to (cutoff as in uhnsw_search_opts, 0 => 1.4).  counts / K is the recall
+ * that verifying the true top-t base-metric points would reach.
+ *   q, p     device, nq x d and [nq]
+ *   counts   device int32 [nq][t_max]; 1 <= K <= t_max <= 256
+ * Allocates its scratch with cudaMalloc and returns after `stream` has
+ * synchronised.  Errors: EINVAL, ECUDA.
+ */
+int uhnsw_idealized_recall(uhnsw_index* idx, const float* q, const float* p, int64_t nq,
+                           int32_t K, int32_t t_max, float cutoff, int32_t* counts, void* stream);
+
+/*
+ * A t per p for a target recall, from idealized-recall curves (host code).
+ * Bin b holds p in (p_lo + b w, p_lo + (b+1) w] (values outside go to the end
+ * bins; a p within 1e-4 w of an upper edge counts as on it); out_t[b] is the smallest t whose mean idealized recall over the
+ * sample queries of that bin reaches `target` (t_max if none does, 0 for an
+ * empty bin).  Pass out_t's entries as uhnsw_search_opts.t_per_query for the
+ * queries of each bin, with tau a little above the target (the paper takes
+ * 0.92 for a target of 0.9).
+ *   counts   host int32 [n][t_max] from uhnsw_idealized_recall; p host [n]
+ * Errors: EINVAL.
+ */
+int uhnsw_plan_t(const int32_t* counts, const float* p, int64_t n, int32_t K, int32_t t_max,
+                 float target, float p_lo, float bin_width, int32_t nbins, int32_t* out_t);
 
 /*
  * uhnsw_exact for callers that cannot allocate device memory.  Such callers

@@ -406,7 +406,8 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
     return fail(UHNSW_EINVAL, "uhnsw_search: stage_bytes=%d not in [0, 65536]", opts.stage_bytes);
 
   int ef_cap;
-  if (ef) ef_cap = opts.ef_max > 0 ? opts.ef_max : UHNSW_MAX_EF;
+  const bool per_query_beam = ef != nullptr || opts.t_per_query != nullptr;
+  if (per_query_beam) ef_cap = opts.ef_max > 0 ? opts.ef_max : UHNSW_MAX_EF;
   else ef_cap = std::max({ef_default, opts.t, k_max});
   if (ef_cap > UHNSW_MAX_EF)
     return fail(UHNSW_EINVAL, "uhnsw_search: beam %d exceeds %d", ef_cap, UHNSW_MAX_EF);
@@ -473,6 +474,8 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   a.t = opts.t;
   a.kappa = opts.kappa;
   a.tau = opts.tau != 0.f ? opts.tau : 0.92f;
+  a.tq = opts.t_per_query;
+  a.tauq = opts.tau_per_query;
   a.cutoff = opts.cutoff > 0.f ? opts.cutoff : 1.4f;
   a.mode = opts.verify_mode;
   a.width = width;
@@ -534,7 +537,7 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
     // beam buckets <= 64, 128, 256, 512, capped at ef_cap (one bucket when
     // every query has the same ef)
     P->bb.n = 0;
-    if (ef)
+    if (per_query_beam)
       for (int bound : {64, 128, 256, 512})
         if (bound < ef_cap) P->bb.bound[P->bb.n++] = bound;
     P->bb.bound[P->bb.n++] = ef_cap;
@@ -665,11 +668,14 @@ extern "C" int uhnsw_search_host(uhnsw_index* idx, const float* q, const float* 
   if (nq == 0) return UHNSW_OK;
   if (!q || !p || !out_ids || !out_dist) return fail(UHNSW_EINVAL, "uhnsw_search_host: NULL pointer");
   if (k_max < 1 || k_max > UHNSW_MAX_EF) return fail(UHNSW_EINVAL, "uhnsw_search_host: k_max");
+  const int32_t* ht = opts ? opts->t_per_query : nullptr;    // host arrays here
+  const float* htau = opts ? opts->tau_per_query : nullptr;
   const size_t bq = (size_t)nq * idx->d * 4, bp = (size_t)nq * 4, bk = k ? (size_t)nq * 4 : 0,
                be = ef ? (size_t)nq * 4 : 0, bi = (size_t)nq * k_max * 8,
-               bd = (size_t)nq * k_max * 4;
+               bd = (size_t)nq * k_max * 4, bt = ht ? (size_t)nq * 4 : 0,
+               bta = htau ? (size_t)nq * 4 : 0;
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-  const size_t need = al(bq) + al(bp) + al(bk) + al(be) + al(bi) + al(bd);
+  const size_t need = al(bq) + al(bp) + al(bk) + al(be) + al(bi) + al(bd) + al(bt) + al(bta);
   std::lock_guard<std::mutex> lock(idx->mu);
   if (need > idx->stage_bytes) {
     cudaFree(idx->stage);
@@ -685,12 +691,16 @@ extern "C" int uhnsw_search_host(uhnsw_index* idx, const float* q, const float* 
   int32_t* dk = k ? (int32_t*)s : nullptr; s += al(bk);
   int32_t* de = ef ? (int32_t*)s : nullptr; s += al(be);
   int64_t* di = (int64_t*)s; s += al(bi);
-  float* dd = (float*)s;
+  float* dd = (float*)s; s += al(bd);
+  int32_t* dt = ht ? (int32_t*)s : nullptr; s += al(bt);
+  float* dta = htau ? (float*)s : nullptr;
   Prepared P;
   uhnsw_search_opts o2;
   std::memset(&o2, 0, sizeof(o2));
   if (opts) o2 = *opts;
   o2.use_graph = 0;
+  o2.t_per_query = dt;
+  o2.tau_per_query = dta;
   int rc = prepare_search(idx, dq, dp, dk, de, nq, k_max, ef_default, &o2, di, dd, &P);
   if (rc != UHNSW_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
@@ -698,6 +708,8 @@ extern "C" int uhnsw_search_host(uhnsw_index* idx, const float* q, const float* 
   if (e == cudaSuccess) e = cudaMemcpyAsync(dp, p, bp, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && k) e = cudaMemcpyAsync(dk, k, bk, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && ef) e = cudaMemcpyAsync(de, ef, be, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && ht) e = cudaMemcpyAsync(dt, ht, bt, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && htau) e = cudaMemcpyAsync(dta, htau, bta, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search_host: upload");
   rc = enqueue_search(idx, P, st);
   if (rc != UHNSW_OK) return rc;
@@ -776,6 +788,85 @@ extern "C" int uhnsw_exact(uhnsw_index* idx, const float* q, const float* p, int
   cudaError_t e = launch_exact(idx->base32, idx->n, idx->d, idx->d_pad, q, p, nq, k, ns, pd, pi,
                                out_ids, out_dist, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "uhnsw_exact: launch");
+  return UHNSW_OK;
+}
+
+extern "C" int uhnsw_idealized_recall(uhnsw_index* idx, const float* q, const float* p,
+                                      int64_t nq, int32_t K, int32_t t_max, float cutoff,
+                                      int32_t* counts, void* stream) {
+  clear_error();
+  if (!idx) return fail(UHNSW_EINVAL, "uhnsw_idealized_recall: index is NULL");
+  if (nq < 0 || nq > INT32_MAX / 2) return fail(UHNSW_EINVAL, "uhnsw_idealized_recall: nq");
+  if (K < 1 || t_max < K || t_max > 256)
+    return fail(UHNSW_EINVAL, "uhnsw_idealized_recall: need 1 <= K <= t_max <= 256 (K=%d, t_max=%d)",
+                K, t_max);
+  if (!(cutoff >= 0.f) || !std::isfinite(cutoff))
+    return fail(UHNSW_EINVAL, "uhnsw_idealized_recall: cutoff");
+  if (nq > 0 && (!q || !p || !counts)) return fail(UHNSW_EINVAL, "uhnsw_idealized_recall: NULL pointer");
+  if (nq == 0) return UHNSW_OK;
+  const float cut = cutoff > 0.f ? cutoff : 1.4f;
+  const int ns = std::max(exact_workspace_slices(idx->n, nq, K, idx->num_sms),
+                          exact_workspace_slices(idx->n, nq, t_max, idx->num_sms));
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t b_ik = (size_t)nq * K * 8, b_dk = (size_t)nq * K * 4;
+  const size_t b_it = (size_t)nq * t_max * 8, b_dt = (size_t)nq * t_max * 4;
+  const size_t b_pb = (size_t)nq * 4, b_ws = (size_t)ns * nq * t_max * 8;
+  const size_t need = al(b_ik) + al(b_dk) + al(b_it) + al(b_dt) + al(b_pb) + al(b_ws);
+  char* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, need);
+  if (e != cudaSuccess) return cuda_fail(e, "uhnsw_idealized_recall: scratch");
+  char* s = buf;
+  int64_t* ik = (int64_t*)s; s += al(b_ik);
+  float* dk = (float*)s; s += al(b_dk);
+  int64_t* it = (int64_t*)s; s += al(b_it);
+  float* dt = (float*)s; s += al(b_dt);
+  float* pb = (float*)s; s += al(b_pb);
+  float* pd = (float*)s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const float gp0 = (float)base_metric_p(idx->gmetric[0]), gp1 = (float)base_metric_p(idx->gmetric[1]);
+  // exact L_p top-K, exact base-metric top-t_max, then the curves
+  e = launch_exact(idx->base32, idx->n, idx->d, idx->d_pad, q, p, nq, K, ns, pd,
+                   (int32_t*)((char*)pd + (size_t)ns * nq * K * 4), ik, dk, st);
+  if (e == cudaSuccess) e = launch_base_p(p, nq, gp0, gp1, cut, pb, st);
+  if (e == cudaSuccess)
+    e = launch_exact(idx->base32, idx->n, idx->d, idx->d_pad, q, pb, nq, t_max, ns, pd,
+                     (int32_t*)((char*)pd + (size_t)ns * nq * t_max * 4), it, dt, st);
+  if (e == cudaSuccess) e = launch_recall_curve(ik, it, nq, K, t_max, counts, st);
+  cudaError_t e2 = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return cuda_fail(e, "uhnsw_idealized_recall: run");
+  return UHNSW_OK;
+}
+
+extern "C" int uhnsw_plan_t(const int32_t* counts, const float* p, int64_t n, int32_t K,
+                            int32_t t_max, float target, float p_lo, float bin_width,
+                            int32_t nbins, int32_t* out_t) {
+  clear_error();
+  if (n < 0 || K < 1 || t_max < K || nbins < 1 || !(bin_width > 0.f) || !(target > 0.f) ||
+      !(target <= 1.f) || (n > 0 && (!counts || !p)) || !out_t)
+    return fail(UHNSW_EINVAL, "uhnsw_plan_t: bad argument");
+  std::vector<double> sum((size_t)nbins * t_max, 0.0);
+  std::vector<int64_t> cnt(nbins, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    // bin b holds p in (p_lo + b w, p_lo + (b + 1) w]; values outside go to the end
+    // bins.  A p within 1e-4 bin widths of an upper edge counts as on it, so
+    // that FP32 values of grid points (0.6f is above 0.6) fall in their bin.
+    int b = (int)std::ceil((double)(p[i] - p_lo) / bin_width - 1e-4) - 1;
+    b = std::min(std::max(b, 0), nbins - 1);
+    ++cnt[b];
+    for (int t = 0; t < t_max; ++t) sum[(size_t)b * t_max + t] += counts[i * t_max + t];
+  }
+  for (int b = 0; b < nbins; ++b) {
+    out_t[b] = 0;
+    if (!cnt[b]) continue;
+    out_t[b] = t_max;
+    for (int t = 0; t < t_max; ++t)
+      if (sum[(size_t)b * t_max + t] / ((double)cnt[b] * K) >= (double)target) {
+        out_t[b] = t + 1;
+        break;
+      }
+  }
   return UHNSW_OK;
 }
 

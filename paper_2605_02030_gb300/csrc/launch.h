@@ -63,6 +63,11 @@ cudaError_t launch_convert(const float* src, void* dst, uhnsw_dtype dt, int64_t 
 cudaError_t launch_inexact_count(const float* src, const void* dst, uhnsw_dtype dt, int64_t count,
                                  unsigned long long* bad, cudaStream_t st);
 
+// Idealized-recall curves (idealized.cu).
+cudaError_t launch_base_p(const float* p, int64_t nq, float gp0, float gp1, float cutoff,
+                          float* out, cudaStream_t st);
+cudaError_t launch_recall_curve(const int64_t* ids_k, const int64_t* ids_t, int64_t nq, int K,
+                                int T, int32_t* counts, cudaStream_t st);
 int exact_workspace_slices(int64_t n, int64_t nq, int k, int num_sms);
 cudaError_t launch_exact(const float* base, int64_t n, int d, int d_pad, const float* q,
                          const float* p, int64_t nq, int k, int nslices, float* part_d,

@@ -67,6 +67,8 @@ struct QueryArgs {
   int32_t t;            // 0 => ef
   int32_t kappa;        // 0 => k
   float tau, cutoff;
+  const int32_t* tq;    // [nq] per-query t, or null (t)
+  const float* tauq;    // [nq] per-query tau (0 => 0.92), or null (tau)
   int32_t mode;         // uhnsw_verify_mode
   int32_t width;        // beam entries expanded per step
   int32_t hash_bits;    // visited table holds 1 << hash_bits slots
@@ -100,6 +102,16 @@ struct Route {
 __device__ __forceinline__ Route route_query(const QueryArgs& a, float p) {
   const int slot = p == a.gp[0] ? 0 : p == a.gp[1] ? 1 : (p <= a.cutoff ? 0 : 1);
   return Route{slot, p == a.gp[slot], a.gmetric[slot]};
+}
+
+// t and tau of query qi (per-query arrays when given).
+__device__ __forceinline__ int query_t(const QueryArgs& a, int64_t qi) {
+  return a.tq ? a.tq[qi] : a.t;
+}
+__device__ __forceinline__ float query_tau(const QueryArgs& a, int64_t qi) {
+  if (!a.tauq) return a.tau;
+  const float v = a.tauq[qi];
+  return v != 0.f ? v : 0.92f;
 }
 
 // The distance a direct query returns: the base sum's root S^(1/p_base).
@@ -356,8 +368,8 @@ __device__ __forceinline__ void verify_fold(int k, const VerifyBufs& vb, BlockSc
 // left in (vb.td[cur], vb.ti[cur]) with s.tn entries.
 template <int BLOCK, int PM>
 __device__ void verify_run(const QueryArgs& a, const float* qs, float p, const uint32_t* C, int t,
-                           int k, int kappa, bool exact, const VerifyBufs& vb, BlockScalars& s,
-                           int& cur) {
+                           int k, int kappa, float tau, bool exact, const VerifyBufs& vb,
+                           BlockScalars& s, int& cur) {
   constexpr int NVT = BLOCK / 8;
   const float kInf = __int_as_float(0x7f800000);
   if (threadIdx.x == 0) {
@@ -399,23 +411,23 @@ __device__ void verify_run(const QueryArgs& a, const float* qs, float p, const u
     const int ov = s.overlap;
     for (int j = threadIdx.x; j < s.tn; j += BLOCK) vb.ti[cur][j] &= kIdMask;
     __syncthreads();
-    if ((float)ov / (float)k >= a.tau) break;
+    if ((float)ov / (float)k >= tau) break;
   }
 }
 
 template <int BLOCK>
 __device__ __forceinline__ void verify_dispatch(const QueryArgs& a, const float* qs, float p,
                                                 const uint32_t* C, int t, int k, int kappa,
-                                                bool exact, const VerifyBufs& vb, BlockScalars& s,
-                                                int& cur) {
+                                                float tau, bool exact, const VerifyBufs& vb,
+                                                BlockScalars& s, int& cur) {
   switch (pmode_of(p)) {
-    case kPOne: verify_run<BLOCK, kPOne>(a, qs, p, C, t, k, kappa, exact, vb, s, cur); break;
-    case kPTwo: verify_run<BLOCK, kPTwo>(a, qs, p, C, t, k, kappa, exact, vb, s, cur); break;
-    case kPHalf: verify_run<BLOCK, kPHalf>(a, qs, p, C, t, k, kappa, exact, vb, s, cur); break;
+    case kPOne: verify_run<BLOCK, kPOne>(a, qs, p, C, t, k, kappa, tau, exact, vb, s, cur); break;
+    case kPTwo: verify_run<BLOCK, kPTwo>(a, qs, p, C, t, k, kappa, tau, exact, vb, s, cur); break;
+    case kPHalf: verify_run<BLOCK, kPHalf>(a, qs, p, C, t, k, kappa, tau, exact, vb, s, cur); break;
     case kPThreeHalves:
-      verify_run<BLOCK, kPThreeHalves>(a, qs, p, C, t, k, kappa, exact, vb, s, cur);
+      verify_run<BLOCK, kPThreeHalves>(a, qs, p, C, t, k, kappa, tau, exact, vb, s, cur);
       break;
-    default: verify_run<BLOCK, kPGeneral>(a, qs, p, C, t, k, kappa, exact, vb, s, cur); break;
+    default: verify_run<BLOCK, kPGeneral>(a, qs, p, C, t, k, kappa, tau, exact, vb, s, cur); break;
   }
 }
 
@@ -502,11 +514,12 @@ __device__ void run_query(const QueryArgs& a, int64_t qi, unsigned char* smem, c
   const Route rt = route_query(a, p);
   const bool direct = rt.direct;
   const int metric = rt.metric;
-  int tt = direct ? k : (a.t > 0 ? a.t : ef);
+  const int tq = query_t(a, qi);
+  int tt = direct ? k : (tq > 0 ? tq : ef);
   if (tt < k) tt = k;
   const int efp = max(ef, tt);
   const GraphDev& g = a.g[rt.slot];
-  const bool ok = (p > 0.f) && (p <= 2.f) && k >= 1 && k <= a.k_max && ef >= 1 &&
+  const bool ok = (p > 0.f) && (p <= 2.f) && k >= 1 && k <= a.k_max && ef >= 1 && tq >= 0 &&
                   efp <= a.ef_cap && g.ell0 != nullptr && a.width * g.deg0 <= a.cmax &&
                   g.deg <= a.cmax;
   if (!ok) {
@@ -686,7 +699,7 @@ __device__ void run_query(const QueryArgs& a, int64_t qi, unsigned char* smem, c
   vb.si = si;
   int vc = 0;
   const int kappa = a.kappa > 0 ? a.kappa : k;
-  verify_dispatch<BLOCK>(a, qs, p, bi[cb], nc, k, kappa, direct, vb, s, vc);
+  verify_dispatch<BLOCK>(a, qs, p, bi[cb], nc, k, kappa, query_tau(a, qi), direct, vb, s, vc);
   write_verified<BLOCK>(a, qi, p, k, vb, s, vc);
   write_stats(a, qi, nb, s.np, s.terms, nexp, nres, 0, rt.slot + 1, nadj);
 }
@@ -768,7 +781,7 @@ __global__ void __launch_bounds__(BLOCK) uhnsw_verify_kernel(const QueryArgs a) 
   vb.si = reinterpret_cast<uint32_t*>(smem + L.si);
   int vc = 0;
   const int kappa = a.kappa > 0 ? a.kappa : k;
-  verify_dispatch<BLOCK>(a, qs, p, cv, tv, k, kappa, false, vb, s, vc);
+  verify_dispatch<BLOCK>(a, qs, p, cv, tv, k, kappa, a.tau, false, vb, s, vc);
   write_verified<BLOCK>(a, qi, p, k, vb, s, vc);
   write_stats(a, qi, 0, s.np, s.terms, 0, 0, 0, 0, 0);
 }

@@ -142,6 +142,8 @@ int launch_batch(uhnsw_server* s, Lane& L, int device) {
   so.use_graph = 0;
   so.persistent = 0;  // the index's queue counter serves one persistent search at a time
   so.kernel_events = nullptr;
+  so.t_per_query = nullptr;  // per-request t / tau are not part of a server request
+  so.tau_per_query = nullptr;
   so.ef_max = s->o.ef_max;
   int rc = uhnsw_search(s->idx, L.d_q, L.d_p, L.d_k, L.d_ef, nb, s->o.k_max, s->o.ef_max, &so,
                         L.d_ids, L.d_dist, L.stream);

@@ -94,26 +94,29 @@ __device__ __forceinline__ int query_route(float p, float cutoff, float gp0, flo
 }
 
 __device__ __forceinline__ int query_bin(const BeamBuckets& bb, const float* p, const int32_t* k,
-                                         const int32_t* ef, int64_t i, int k_max, int ef_default,
-                                         int t, float cutoff, float gp0, float gp1) {
+                                         const int32_t* ef, const int32_t* tq, int64_t i,
+                                         int k_max, int ef_default, int t, float cutoff, float gp0,
+                                         float gp1) {
   const bool direct = p[i] == gp0 || p[i] == gp1;
-  const int b = beam_bucket(bb, query_beam(direct, k ? k[i] : k_max, ef ? ef[i] : ef_default, t));
+  const int b = beam_bucket(bb, query_beam(direct, k ? k[i] : k_max, ef ? ef[i] : ef_default,
+                                           tq ? tq[i] : t));
   return b * kRoutes + query_route(p[i], cutoff, gp0, gp1);
 }
 
 // Counting sort of the query indices by (beam bucket, route): counts, then
 // slots.  ws[0..64): counts per bin, ws[64..128): cursors; info[2b] = first
 // slot of bucket b, info[2b+1] = its count.
-__global__ void bucket_count_kernel(const float* p, const int32_t* k, const int32_t* ef, int64_t nq,
+__global__ void bucket_count_kernel(const float* p, const int32_t* k, const int32_t* ef,
+                                    const int32_t* tq, int64_t nq,
                                     int k_max, int ef_default, int t, float cutoff, float gp0,
                                     float gp1, BeamBuckets bb, int32_t* ws) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq;
        i += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&ws[query_bin(bb, p, k, ef, i, k_max, ef_default, t, cutoff, gp0, gp1)], 1);
+    atomicAdd(&ws[query_bin(bb, p, k, ef, tq, i, k_max, ef_default, t, cutoff, gp0, gp1)], 1);
 }
 
 __global__ void bucket_scatter_kernel(const float* p, const int32_t* k, const int32_t* ef,
-                                      int64_t nq, int k_max, int ef_default, int t, float cutoff,
+                                      const int32_t* tq, int64_t nq, int k_max, int ef_default, int t, float cutoff,
                                       float gp0, float gp1, BeamBuckets bb, int32_t* ws,
                                       int32_t* order, int32_t* info) {
   if (blockIdx.x == 0 && threadIdx.x < bb.n) {
@@ -126,7 +129,7 @@ __global__ void bucket_scatter_kernel(const float* p, const int32_t* k, const in
   }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int bin = query_bin(bb, p, k, ef, i, k_max, ef_default, t, cutoff, gp0, gp1);
+    const int bin = query_bin(bb, p, k, ef, tq, i, k_max, ef_default, t, cutoff, gp0, gp1);
     int base = 0;
     for (int j = 0; j < bin; ++j) base += ws[j];
     const int pos = atomicAdd(&ws[kBins + bin], 1);
@@ -140,12 +143,12 @@ cudaError_t launch_bucketing(const QueryArgs& a, const BeamBuckets& bb, int32_t*
   if (e != cudaSuccess) return e;
   int64_t blocks = (a.nq + 255) / 256;
   if (blocks > 1024) blocks = 1024;
-  bucket_count_kernel<<<(unsigned)blocks, 256, 0, st>>>(a.p, a.k, a.ef, a.nq, a.k_max,
+  bucket_count_kernel<<<(unsigned)blocks, 256, 0, st>>>(a.p, a.k, a.ef, a.tq, a.nq, a.k_max,
                                                          a.ef_default, a.t, a.cutoff, a.gp[0],
                                                          a.gp[1], bb, ws);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  bucket_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(a.p, a.k, a.ef, a.nq, a.k_max,
+  bucket_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(a.p, a.k, a.ef, a.tq, a.nq, a.k_max,
                                                            a.ef_default, a.t, a.cutoff, a.gp[0],
                                                            a.gp[1], bb, ws, order, info);
   return cudaGetLastError();

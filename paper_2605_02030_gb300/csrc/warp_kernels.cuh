@@ -414,7 +414,8 @@ __device__ __forceinline__ void warp_verify_range(const QueryArgs& a, const floa
 // One call site of warp_verify_range per p form keeps the kernel's code small.
 __device__ __forceinline__ void warp_verify_run(const QueryArgs& a, const float* qs, float p,
                                                 const uint32_t* C, int t, int k, int kappa,
-                                                bool exact, unsigned char* stage, WarpVerify& v) {
+                                                float tau, bool exact, unsigned char* stage,
+                                                WarpVerify& v) {
   const int lane = threadIdx.x & 31;
   const int pm = pmode_of(p);
   v.tn = 0;
@@ -437,7 +438,7 @@ __device__ __forceinline__ void warp_verify_run(const QueryArgs& a, const float*
       for (int off = 16; off > 0; off >>= 1) ov += __shfl_xor_sync(kFull, ov, off);
       for (int j = lane; j < v.tn; j += 32) v.ci_()[j] &= kIdMask;
       __syncwarp();
-      if ((float)ov / (float)k >= a.tau) break;
+      if ((float)ov / (float)k >= tau) break;
     }
   }
 }
@@ -467,11 +468,12 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
   const Route rt = route_query(a, p);
   const bool direct = rt.direct;
   const int metric = rt.metric;
-  int tt = direct ? k : (a.t > 0 ? a.t : ef);
+  const int tq = query_t(a, qi);
+  int tt = direct ? k : (tq > 0 ? tq : ef);
   if (tt < k) tt = k;
   const int efp = max(ef, tt);
   const GraphDev g = rt.slot == 0 ? a.g[0] : a.g[1];
-  const bool ok = (p > 0.f) && (p <= 2.f) && k >= 1 && k <= a.k_max && ef >= 1 &&
+  const bool ok = (p > 0.f) && (p <= 2.f) && k >= 1 && k <= a.k_max && ef >= 1 && tq >= 0 &&
                   efp <= a.ef_cap && g.ell0 != nullptr && a.width * g.deg0 <= a.cmax &&
                   g.deg <= a.cmax;
   if (!ok) {
@@ -668,7 +670,7 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
   v.sd = sd;
   v.si = si;
   const int kappa = a.kappa > 0 ? a.kappa : k;
-  warp_verify_run(a, qs, p, bic, nc, k, kappa, direct, stage, v);
+  warp_verify_run(a, qs, p, bic, nc, k, kappa, query_tau(a, qi), direct, stage, v);
   const double inv_p = 1.0 / (double)p;
   for (int j = lane; j < a.k_max; j += 32) {
     if (j < k && j < v.tn) {

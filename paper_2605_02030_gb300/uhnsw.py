@@ -70,10 +70,13 @@ class _SearchOpts(C.Structure):
         ("stage_bytes", C.c_int32),
         ("team_lanes", C.c_int32),
         ("kernel_events", C.c_void_p),
+        ("t_per_query", C.c_void_p),
+        ("tau_per_query", C.c_void_p),
     ]
 
 
 EXPORTS = ("uhnsw_load", "uhnsw_search", "uhnsw_search_host", "uhnsw_verify", "uhnsw_exact",
+           "uhnsw_idealized_recall", "uhnsw_plan_t",
            "uhnsw_exact_static", "uhnsw_server_create", "uhnsw_server_submit", "uhnsw_server_poll",
            "uhnsw_server_wait", "uhnsw_server_replay", "uhnsw_server_stats",
            "uhnsw_server_destroy", "uhnsw_autotune", "uhnsw_autotune_save", "uhnsw_autotune_load",
@@ -107,6 +110,10 @@ def load_library():
     lib.uhnsw_verify.argtypes = [P, P, P, P, I32, I32, I64, P, P, P, P]
     lib.uhnsw_exact.restype = C.c_int
     lib.uhnsw_exact.argtypes = [P, P, P, I64, I32, P, P, P]
+    lib.uhnsw_idealized_recall.restype = C.c_int
+    lib.uhnsw_idealized_recall.argtypes = [P, P, P, I64, I32, I32, C.c_float, P, P]
+    lib.uhnsw_plan_t.restype = C.c_int
+    lib.uhnsw_plan_t.argtypes = [P, P, I64, I32, I32, C.c_float, C.c_float, C.c_float, I32, P]
     lib.uhnsw_exact_static.restype = C.c_int
     lib.uhnsw_exact_static.argtypes = [P, P, P, I64, I32, P, P, P]
     lib.uhnsw_index_info.restype = C.c_int
@@ -229,6 +236,20 @@ def _graph_struct(g: dict | None):
     return s, keep
 
 
+# ----------------------------------------------------------------- t per p
+def plan_t(counts: np.ndarray, p: np.ndarray, K: int, target: float, p_lo: float = 0.5,
+           bin_width: float = 0.1, nbins: int = 15) -> np.ndarray:
+    """uhnsw_plan_t: the smallest t per p bin whose mean idealized recall reaches
+    `target` (bin b holds p in (p_lo + b w, p_lo + (b + 1) w])."""
+    counts = np.ascontiguousarray(counts, np.int32)
+    p = np.ascontiguousarray(p, np.float32)
+    out = np.zeros(nbins, np.int32)
+    _check(load_library().uhnsw_plan_t(_np_ptr(counts), _np_ptr(p), counts.shape[0], int(K),
+                                       counts.shape[1], float(target), float(p_lo),
+                                       float(bin_width), int(nbins), _np_ptr(out)))
+    return out
+
+
 # ----------------------------------------------------------------- index
 class Index:
     """A loaded U-HNSW index (base vectors + two graphs) on the current CUDA
@@ -271,13 +292,14 @@ class Index:
         o.stats = stats_t.data_ptr() if stats_t is not None else None
         return o
 
-    def search(self, q, p, k=10, ef=64, *, k_max: int | None = None, t: int = 0, tau: float = 0.0,
+    def search(self, q, p, k=10, ef=64, *, k_max: int | None = None, t=0, tau=0.0,
                kappa: int = 0, cutoff: float = 0.0, mode: str = "exact", width: int = 1,
                persistent: bool = False, use_graph: bool = False, ef_max: int = 0,
                query_threads: int = 0, stage_bytes: int = 0, team_lanes: int = 0,
                stats: bool = False, out=None, stream=None, kernel_events=None):
         """Algorithm 1 on device tensors.  q: float32 [nq, d] cuda; p: float32 [nq];
-        k / ef: int (same for all) or int32 [nq] tensors.  kernel_events: two
+        k / ef / t: int (same for all) or int32 [nq] tensors; tau: float or
+        float32 [nq] tensor.  kernel_events: two
         torch.cuda.Event (already recorded once) bracketing the search kernels
         alone.  Returns (ids int64 [nq, k_max], dist float32 [nq, k_max], stats
         int32 [nq, 8] or None)."""
@@ -298,8 +320,13 @@ class Index:
         else:
             ids, dist = out
         st = torch.zeros((nq, NSTATS), dtype=torch.int32, device=q.device) if stats else None
-        o = self._opts(t, kappa, tau, cutoff, mode, width, persistent, use_graph, ef_max, st,
-                       query_threads, stage_bytes, team_lanes)
+        t_t = t if torch.is_tensor(t) else None
+        tau_t = tau if torch.is_tensor(tau) else None
+        o = self._opts(0 if t_t is not None else t, kappa, 0.0 if tau_t is not None else tau,
+                       cutoff, mode, width, persistent, use_graph, ef_max, st, query_threads,
+                       stage_bytes, team_lanes)
+        o.t_per_query = t_t.data_ptr() if t_t is not None else None
+        o.tau_per_query = tau_t.data_ptr() if tau_t is not None else None
         if kernel_events is not None:
             evs = (C.c_void_p * 2)(*(int(e.cuda_event) for e in kernel_events))
             if not evs[0] or not evs[1]:
@@ -329,9 +356,15 @@ class Index:
             dist = np.empty((nq, k_max), np.float32)
         else:
             ids, dist = out
+        t_a = (np.ascontiguousarray(kw.pop("t"), np.int32)
+               if isinstance(kw.get("t"), np.ndarray) else None)
+        tau_a = (np.ascontiguousarray(kw.pop("tau"), np.float32)
+                 if isinstance(kw.get("tau"), np.ndarray) else None)
         o = self._opts(**{x: kw[x] for x in ("t", "kappa", "tau", "cutoff", "mode", "width",
                                              "persistent", "ef_max", "query_threads",
                                              "stage_bytes", "team_lanes") if x in kw})
+        o.t_per_query = t_a.ctypes.data if t_a is not None else None
+        o.tau_per_query = tau_a.ctypes.data if tau_a is not None else None
         _check(lib.uhnsw_search_host(self._h, _np_ptr(q), _np_ptr(p), _np_ptr(k_a), _np_ptr(ef_a),
                                      nq, k_max, ef_default, C.byref(o), _np_ptr(ids),
                                      _np_ptr(dist), _stream_ptr(stream)))
@@ -350,6 +383,17 @@ class Index:
         _check(lib.uhnsw_verify(self._h, _t_ptr(q), _t_ptr(p), _t_ptr(cand), t, k, nq, C.byref(o),
                                 _t_ptr(ids), _t_ptr(dist), _stream_ptr(stream)))
         return ids, dist, st
+
+    def idealized_recall(self, q, p, K: int, t_max: int, cutoff: float = 0.0, stream=None):
+        """uhnsw_idealized_recall: int32 [nq, t_max] tensor of |top-K under L_p of
+        each query & top-t under its graph's base metric| for t = 1 .. t_max."""
+        import torch
+        lib = load_library()
+        counts = torch.empty((q.shape[0], t_max), dtype=torch.int32, device=q.device)
+        _check(lib.uhnsw_idealized_recall(self._h, _t_ptr(q), _t_ptr(p), q.shape[0], int(K),
+                                          int(t_max), float(cutoff), _t_ptr(counts),
+                                          _stream_ptr(stream)))
+        return counts
 
     def exact(self, q, p, k: int, stream=None):
         """Exhaustive L_p k-NN on the GPU: (ids int64 [nq, k], dist float32 [nq, k])."""

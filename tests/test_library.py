@@ -151,3 +151,27 @@ def test_builder_parallel_invariants(lib):
 
     g1 = U.build_graph(base, 2, w.M, w.ef_construction, lv, threads=1)
     assert reach(g) >= reach(g1) - 0.01
+
+
+def test_plan_t_picks_the_smallest_t_per_p_bin(lib):
+    """uhnsw_plan_t on hand-made idealized-recall counts (K = 4, t_max = 6):
+    the smallest t whose mean count over a bin's queries reaches target * K."""
+    counts = np.array([[1, 2, 3, 4, 4, 4],     # p = 0.55 -> bin 0
+                       [0, 1, 2, 2, 3, 4],     # p = 0.58 -> bin 0
+                       [2, 4, 4, 4, 4, 4],     # p = 0.75 -> bin 2
+                       [0, 0, 0, 1, 1, 2]],    # p = 1.95 -> bin 14
+                      np.int32)
+    p = np.array([0.55, 0.58, 0.75, 1.95], np.float32)
+    # bin 0 means: 0.5, 1.5, 2.5, 3, 3.5, 4 (out of 4)
+    np.testing.assert_array_equal(U.plan_t(counts, p, 4, 0.75)[[0, 1, 2, 14]], [4, 0, 2, 6])
+    np.testing.assert_array_equal(U.plan_t(counts, p, 4, 0.875)[[0, 2]], [5, 2])
+    np.testing.assert_array_equal(U.plan_t(counts, p, 4, 1.0)[[0, 2, 14]], [6, 2, 6])
+    # p at a bin's upper edge belongs to that bin; below p_lo goes to bin 0
+    out = U.plan_t(counts[:1], np.array([0.6], np.float32), 4, 1.0)
+    assert out[0] == 4 and out[1] == 0
+    out = U.plan_t(counts[:1], np.array([0.1], np.float32), 4, 1.0)
+    assert out[0] == 4
+    with pytest.raises(U.UHNSWError):
+        U.plan_t(counts, p, 4, 1.5)
+    with pytest.raises(U.UHNSWError):
+        U.plan_t(counts, p, 7, 0.5)          # K above t_max
