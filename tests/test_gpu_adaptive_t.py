@@ -95,8 +95,10 @@ def test_per_query_t_and_tau_equal_scalar_calls(U, sift_case, mode, persistent):
 
 def test_planned_t_meets_its_idealized_target(U, sift_case):
     """End to end: curves on the queries, a t per p bin for a 0.95 target,
-    then a search with those t (exact verification, beam ef' = max(ef, t)):
-    recall against the exact answer stays near the target."""
+    then a search with those t (exact verification, beam ef' = max(ef, t)).
+    The curves assume the true base-metric top-t; the search finds an
+    approximation of it, so the beam must be good on its own (ef = 48 here;
+    ef = 16 on this small graph reaches only 0.63)."""
     w, base, qs, p, g1, g2 = sift_case
     idx = U.Index(base, g1, g2, traverse_dtype="f16")
     counts = idx.idealized_recall(dev(qs), dev(p), 10, 128).cpu().numpy()
@@ -104,7 +106,7 @@ def test_planned_t_meets_its_idealized_target(U, sift_case):
     assert ((table >= 10) | (table == 0)).all() and table.max() <= 128
     b = np.clip(np.ceil((p - 0.5) / 0.1 - 1e-4).astype(int) - 1, 0, 14)
     tq = table[b].astype(np.int32)
-    ids, _, _ = idx.search(dev(qs), dev(p), k=10, ef=16, t=dev(tq), ef_max=128)
+    ids, _, _ = idx.search(dev(qs), dev(p), k=10, ef=48, t=dev(tq), ef_max=128)
     gt, _ = oracle.exact_knn(base, qs, p, 10)
     ids = ids.cpu().numpy()
     rec = np.mean([len(set(ids[i].tolist()) & set(gt[i].tolist())) / 10 for i in range(len(qs))])
