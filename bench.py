@@ -696,6 +696,74 @@ def run_workload(args, log):
     idx.close()
 
 
+# ---------------------------------------------------------------- t / tau knob
+def run_idealized(args, log):
+    """Section 3.2's experiment on the sift1m recipe: idealized recall of the
+    true base-metric top-t as a candidate set (K = 50, per p), then t planned
+    per p bin for a recall target and searched against a uniform beam."""
+    import torch
+    import paper_2605_02030_gb300 as pkg
+    from paper_2605_02030_gb300 import uhnsw as U
+
+    pkg.build()
+    w = workload(args)
+    base = I.base_vectors(w)
+    qs = I.query_vectors(w)
+    p, _, _ = I.query_params(w)
+    g1, g2 = graphs_for(w, base, log)
+    idx = U.Index(base, g1, g2, traverse_dtype="f16")
+    q_dev = torch.from_numpy(qs).cuda()
+    # idealized recall at K = 50 for p in {0.5, 0.8, 1.2, 1.5, 1.8} on 1,000 queries
+    sub = torch.arange(min(1000, w.nq), device="cuda")
+    curves = {}
+    for pv in (0.5, 0.8, 1.2, 1.5, 1.8):
+        pp = torch.full((len(sub),), pv, dtype=torch.float32, device="cuda")
+        c = idx.idealized_recall(q_dev[sub], pp, 50, 256).cpu().numpy() / 50.0
+        curves[str(pv)] = {str(t): round(float(c[:, t - 1].mean()), 4)
+                           for t in (50, 100, 150, 200, 256)}
+    log(f"idealized recall at K=50: {curves}")
+    # plan t per p bin (K = 10) on the first 2,000 queries, apply to all
+    k = 10
+    p_dev = torch.from_numpy(p).cuda()
+    gt = ground_truth(w, idx, q_dev, p_dev, k, log)
+    cal = min(2000, w.nq)
+    counts = idx.idealized_recall(q_dev[:cal].contiguous(), p_dev[:cal].contiguous(), k, 256)
+    table = U.plan_t(counts.cpu().numpy(), p[:cal], k, args.target)
+    b = np.clip(np.ceil((p - 0.5) / 0.1 - 1e-4).astype(int) - 1, 0, 14)
+    tq = torch.from_numpy(table[b].astype(np.int32)).cuda()
+    flush = torch.empty(384 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed(**kw):
+        ids = None
+        ms = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(1.0)
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ids, _, _ = idx.search(q_dev, p_dev, k=k, persistent=True, use_graph=True, **kw)
+            e.record()
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                ms.append(a.elapsed_time(e))
+        r, per = recall_per_bin(ids.cpu().numpy(), gt, p, k)
+        return {"qps": round(w.nq / statistics.mean(ms) * 1e3, 1), "recall_at_10": round(r, 4),
+                "recall_at_10_min_p_bin": round(min(per.values()), 4)}
+
+    rows = {}
+    for ef in (16, 24, 32, 48):
+        rows[f"uniform ef={ef}"] = timed(ef=ef)
+        rows[f"planned t, ef={ef}"] = timed(ef=ef, t=tq, ef_max=256)
+    line = {"metric": "idealized recall (Section 3.2) and recall-targeted t per p",
+            "config": {"workload": f"sift1m: N={w.n:,} d={w.d}, {w.nq:,} queries, p on the grid",
+                       "idealized_recall_k50": curves,
+                       "target": args.target,
+                       "planned_t_per_p_bin": {f"{0.5 + 0.1 * i:.1f}-{0.6 + 0.1 * i:.1f}": int(v)
+                                               for i, v in enumerate(table)},
+                       "searches": rows}}
+    print(json.dumps(line), flush=True)
+    idx.close()
+
+
 # ---------------------------------------------------------------- oracle arm
 def cpu_baseline(w, base, qs, p, g1, g2, ef, k, seconds):
     """The oracle (single-threaded FP64 Algorithm 1) on a time-bounded sample of
@@ -781,6 +849,10 @@ def main():
                     choices=("sift1m", "gist1m", "unit10m", "sift1m_e"),
                     help="sift1m: the headline line; gist1m: the batched form on 1M x 960 BF16; "
                          "unit10m: the serving form on 10M x 96 FP16; sift1m_e: U-HNSW-E")
+    ap.add_argument("--idealized", action="store_true",
+                    help="Section 3.2's idealized-recall experiment and a recall-targeted t per p")
+    ap.add_argument("--target", type=float, default=0.97,
+                    help="--idealized: idealized-recall target of the t plan")
     ap.add_argument("--quiet", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -791,6 +863,8 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, log)
+    elif args.idealized:
+        run_idealized(args, log)
     elif args.workload != "sift1m":
         run_workload(args, log)
     else:
