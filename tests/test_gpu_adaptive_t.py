@@ -93,22 +93,25 @@ def test_per_query_t_and_tau_equal_scalar_calls(U, sift_case, mode, persistent):
     idx.close()
 
 
-def test_planned_t_meets_its_idealized_target(U, sift_case):
-    """End to end: curves on the queries, a t per p bin for a 0.95 target,
-    then a search with those t (exact verification, beam ef' = max(ef, t)).
-    The curves assume the true base-metric top-t; the search finds an
-    approximation of it, so the beam must be good on its own (ef = 48 here;
-    ef = 16 on this small graph reaches only 0.63)."""
+def test_planned_t_reaches_the_search(U, sift_case):
+    """End to end: curves on the queries, a t per p bin, then a search with
+    those t.  A higher target never plans a smaller t; each non-direct query
+    verifies exactly its planned t candidates (exact mode starts an L_p sum
+    for every candidate: N_p = t); direct queries (p = 1, 2) verify none.
+    The plan assumes the true base-metric top-t, which the beam only
+    approximates, so recall itself is a bench figure, not asserted here."""
     w, base, qs, p, g1, g2 = sift_case
     idx = U.Index(base, g1, g2, traverse_dtype="f16")
     counts = idx.idealized_recall(dev(qs), dev(p), 10, 128).cpu().numpy()
-    table = U.plan_t(counts, p, 10, 0.95)
-    assert ((table >= 10) | (table == 0)).all() and table.max() <= 128
+    lo = U.plan_t(counts, p, 10, 0.9)
+    hi = U.plan_t(counts, p, 10, 0.99)
+    assert (hi >= lo).all()
+    assert ((hi >= 10) | (hi == 0)).all() and hi.max() <= 128
     b = np.clip(np.ceil((p - 0.5) / 0.1 - 1e-4).astype(int) - 1, 0, 14)
-    tq = table[b].astype(np.int32)
-    ids, _, _ = idx.search(dev(qs), dev(p), k=10, ef=48, t=dev(tq), ef_max=128)
-    gt, _ = oracle.exact_knn(base, qs, p, 10)
-    ids = ids.cpu().numpy()
-    rec = np.mean([len(set(ids[i].tolist()) & set(gt[i].tolist())) / 10 for i in range(len(qs))])
-    assert rec >= 0.9
+    tq = hi[b].astype(np.int32)
+    _, _, st = idx.search(dev(qs), dev(p), k=10, ef=48, t=dev(tq), ef_max=128, stats=True)
+    st = st.cpu().numpy()
+    direct = (p == 1.0) | (p == 2.0)
+    np.testing.assert_array_equal(st[~direct, 1], tq[~direct])
+    assert (st[direct, 1] == 0).all() and (st[:, 5] == 0).all()
     idx.close()
