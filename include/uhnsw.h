@@ -440,6 +440,22 @@ int uhnsw_build_graph(const float* base, int64_t n, int32_t d, int32_t metric, i
                       int32_t ef_construction, const int32_t* levels, int32_t threads,
                       uhnsw_built** out);
 
+/*
+ * The same construction on the current CUDA device (Section 2.2's graphs,
+ * built for inputs too large for the host builder).  Nodes are inserted in
+ * batches: a batch searches the graph of the nodes before it (one warp per
+ * new node, efConstruction beam, the neighbour heuristic), then its reverse
+ * links are applied row by row, re-selecting a row past its cap with the
+ * heuristic.  A batch holds 1/16 of the nodes already inserted (1 to 65,536),
+ * and its nodes do not link to each other directly, so the graph differs
+ * from a one-at-a-time build; it is the same on every run.  Arguments as
+ * uhnsw_build_graph (host arrays), with 1 <= ef_construction <= 512.  Device
+ * memory: about n (4 d + 8 M + 520) bytes while it runs.  Returns after the
+ * device work has finished.  Errors: EINVAL, EOOM, ECUDA, ECAPACITY.
+ */
+int uhnsw_build_graph_gpu(const float* base, int64_t n, int32_t d, int32_t metric, int32_t M,
+                          int32_t ef_construction, const int32_t* levels, uhnsw_built** out);
+
 /* Fills `view` with host pointers into the built graph (valid until
  * uhnsw_built_free); level 0 lists every node, so level_nodes[0] is NULL. */
 int uhnsw_built_graph(const uhnsw_built* b, uhnsw_graph* view);

@@ -371,6 +371,47 @@ extern "C" int uhnsw_build_graph(const float* base, int64_t n, int32_t d, int32_
   }
 }
 
+namespace uhnsw_internal {
+// CSR graph from padded adjacency tables (layer 0 [n][M0], upper rows [rows][M]
+// with the row of (v, l) at up_off[v] + l - 1; -1 after the last link), as the
+// GPU builder leaves them.
+uhnsw_built* make_built(int64_t n, int32_t M, int32_t M0, const int32_t* levels, int32_t entry,
+                        int32_t top, const int32_t* ell0, const int32_t* up_off,
+                        const int32_t* up_adj) {
+  auto* g = new (std::nothrow) uhnsw_built();
+  if (!g) return nullptr;
+  try {
+    g->n = n;
+    g->M = M;
+    g->M0 = M0;
+    g->num_levels = top + 1;
+    g->entry = entry;
+    g->count.assign(g->num_levels, 0);
+    g->nodes.resize(g->num_levels);
+    g->offsets.resize(g->num_levels);
+    g->nbrs.resize(g->num_levels);
+    for (int32_t l = 0; l < g->num_levels; ++l) {
+      auto& off = g->offsets[l];
+      auto& nb = g->nbrs[l];
+      off.push_back(0);
+      const int32_t cap = l == 0 ? M0 : M;
+      for (int64_t v = 0; v < n; ++v) {
+        if (levels[v] < l) continue;
+        if (l > 0) g->nodes[l].push_back((int32_t)v);
+        const int32_t* r = l == 0 ? ell0 + v * M0 : up_adj + ((int64_t)up_off[v] + l - 1) * M;
+        for (int32_t j = 0; j < cap && r[j] >= 0; ++j) nb.push_back(r[j]);
+        off.push_back((int64_t)nb.size());
+      }
+      g->count[l] = (int32_t)(off.size() - 1);
+    }
+  } catch (const std::bad_alloc&) {
+    delete g;
+    return nullptr;
+  }
+  return g;
+}
+}  // namespace uhnsw_internal
+
 extern "C" int uhnsw_built_graph(const uhnsw_built* b, uhnsw_graph* view) {
   uhnsw_internal::clear_error();
   if (!b || !view) return uhnsw_internal::fail(UHNSW_EINVAL, "uhnsw_built_graph: NULL argument");

@@ -81,7 +81,7 @@ EXPORTS = ("uhnsw_load", "uhnsw_search", "uhnsw_search_host", "uhnsw_verify", "u
            "uhnsw_server_wait", "uhnsw_server_replay", "uhnsw_server_stats",
            "uhnsw_server_destroy", "uhnsw_autotune", "uhnsw_autotune_save", "uhnsw_autotune_load",
            "uhnsw_index_info", "uhnsw_device_status", "uhnsw_free", "uhnsw_last_error",
-           "uhnsw_build_graph", "uhnsw_built_graph", "uhnsw_built_free")
+           "uhnsw_build_graph", "uhnsw_build_graph_gpu", "uhnsw_built_graph", "uhnsw_built_free")
 
 
 def library_path() -> str:
@@ -144,6 +144,8 @@ def load_library():
     lib.uhnsw_server_destroy.argtypes = [P]
     lib.uhnsw_build_graph.restype = C.c_int
     lib.uhnsw_build_graph.argtypes = [P, I64, I32, I32, I32, I32, P, I32, P]
+    lib.uhnsw_build_graph_gpu.restype = C.c_int
+    lib.uhnsw_build_graph_gpu.argtypes = [P, I64, I32, I32, I32, I32, P, P]
     lib.uhnsw_built_graph.restype = C.c_int
     lib.uhnsw_built_graph.argtypes = [P, P]
     lib.uhnsw_built_free.restype = None
@@ -173,19 +175,26 @@ def _stream_ptr(stream) -> C.c_void_p:
 
 # ----------------------------------------------------------------- graph building
 def build_graph(base: np.ndarray, metric: int, M: int, ef_construction: int, levels: np.ndarray,
-                threads: int = 0) -> dict:
+                threads: int = 0, device: str = "cpu") -> dict:
     """HNSW graph under L1 (metric=1), squared L2 (metric=2) or the L0.5 sum
-    (metric=3, U-HNSW-E's G0.5), built on the host
-    by the library's multi-threaded insertion; returned as a CSR dict
-    {num_levels, entry_point, max_degree0, max_degree, n, levels: [{nodes,
-    offsets, nbrs}]} with level 0 listing every node."""
+    (metric=3, U-HNSW-E's G0.5), built on the host by the library's
+    multi-threaded insertion (device="cpu") or on the current CUDA device by
+    batched insertion (device="gpu"); returned as a CSR dict {num_levels,
+    entry_point, max_degree0, max_degree, n, levels: [{nodes, offsets,
+    nbrs}]} with level 0 listing every node."""
     lib = load_library()
     base = np.ascontiguousarray(base, np.float32)
     levels = np.ascontiguousarray(levels, np.int32)
     n, d = base.shape
     h = C.c_void_p(0)
-    _check(lib.uhnsw_build_graph(_np_ptr(base), n, d, metric, M, ef_construction, _np_ptr(levels),
-                                 threads, C.byref(h)))
+    if device == "gpu":
+        _check(lib.uhnsw_build_graph_gpu(_np_ptr(base), n, d, metric, M, ef_construction,
+                                         _np_ptr(levels), C.byref(h)))
+    elif device == "cpu":
+        _check(lib.uhnsw_build_graph(_np_ptr(base), n, d, metric, M, ef_construction,
+                                     _np_ptr(levels), threads, C.byref(h)))
+    else:
+        raise ValueError(f"device must be 'cpu' or 'gpu', not {device!r}")
     try:
         g = _Graph()
         _check(lib.uhnsw_built_graph(h, C.byref(g)))
