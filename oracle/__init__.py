@@ -107,14 +107,15 @@ def lp_sum(x, q, p: float) -> float:
 
 
 # Base metrics of the graphs (metric codes): 1 = L1, sum |d_j|; 2 = squared
-# L2, sum d_j^2; 3 = L0.5 without its root, sum |d_j|^(1/2).  METRIC_P is the
-# p of each.  U-HNSW uses G1 (L1) and G2 (L2) with cutoff 1.4; U-HNSW-E
+# L2, sum d_j^2; 3 = L0.5 without its root, sum |d_j|^(1/2); 4 = L1.5 without
+# its root, sum |d_j|^(3/2).  METRIC_P is the p of each.  U-HNSW uses G1 (L1) and G2 (L2) with cutoff 1.4; U-HNSW-E
 # (Section 4.6) uses G0.5 (L0.5) and G1 (L1) with cutoff 0.6.
-METRIC_P = {1: 1.0, 2: 2.0, 3: 0.5}
+METRIC_P = {1: 1.0, 2: 2.0, 3: 0.5, 4: 1.5}
 
 
 def base_dist(x, q, metric: int) -> float:
-    """metric 1: sum |d_j| (L1); 2: sum d_j^2 (squared L2); 3: sum |d_j|^(1/2) (L0.5)."""
+    """metric 1: sum |d_j| (L1); 2: sum d_j^2 (squared L2); 3: sum |d_j|^(1/2)
+    (L0.5); 4: sum |d_j|^(3/2) (L1.5)."""
     x, q = _f32(x), _f32(q)
     return _load().oracle_base_dist(_ptr(x), _ptr(q), x.shape[-1], int(metric))
 
@@ -148,7 +149,7 @@ def select_heuristic(base, cand, cand_d, m: int, metric: int):
 
 
 def hnsw_build(base, metric: int, M: int, ef_construction: int, levels, M0: int | None = None):
-    """HNSW graph under L1 (metric=1), L2 (metric=2) or L0.5 (metric=3), as a CSR dict:
+    """HNSW graph under L1 (metric=1), L2 (2), L0.5 (3) or L1.5 (4), as a CSR dict:
     {num_levels, entry_point, max_degree0, max_degree, n,
      levels: [{nodes int32, offsets int64, nbrs int32}, ...]} (level 0 nodes = all ids)."""
     base = _f32(base)

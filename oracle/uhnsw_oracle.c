@@ -37,7 +37,9 @@
  * Order used everywhere: lexicographic (distance, id), ids ascending on ties.
  * Base metrics (metric codes): 1 = L1, sum |d_j|; 2 = the squared L2 sum
  * d_j^2, which orders points exactly like L2; 3 = L0.5 without its root,
- * sum |d_j|^(1/2), which orders points exactly like L0.5.
+ * sum |d_j|^(1/2), which orders points exactly like L0.5; 4 = L1.5 without
+ * its root, sum |d_j|^(3/2) (the fixed-p HNSW graph of Section 4.3 at
+ * p = 1.5, where the paper finds plain HNSW faster).
  */
 #include <math.h>
 #include <stdint.h>
@@ -63,13 +65,14 @@ double oracle_lp_sum(const float* x, const float* q, int32_t d, double p) {
 }
 
 /* Base metric: metric 1 -> L1 sum |d_j|; metric 2 -> squared L2 sum d_j^2;
- * metric 3 -> L0.5 sum |d_j|^(1/2). */
+ * metric 3 -> L0.5 sum |d_j|^(1/2); metric 4 -> L1.5 sum |d_j|^(3/2). */
 double oracle_base_dist(const float* x, const float* q, int32_t d, int32_t metric) {
   double s = 0.0;
   for (int32_t j = 0; j < d; ++j) {
     double diff = (double)x[j] - (double)q[j];
     if (metric == 1) s += fabs(diff);
     else if (metric == 3) s += sqrt(fabs(diff));
+    else if (metric == 4) s += fabs(diff) * sqrt(fabs(diff));
     else s += diff * diff;
   }
   return s;
@@ -77,9 +80,9 @@ double oracle_base_dist(const float* x, const float* q, int32_t d, int32_t metri
 
 /* The p of a base metric, and whether the code is one. */
 static double metric_p(int32_t metric) {
-  return metric == 1 ? 1.0 : metric == 2 ? 2.0 : 0.5;
+  return metric == 1 ? 1.0 : metric == 2 ? 2.0 : metric == 3 ? 0.5 : 1.5;
 }
-static int valid_metric(int32_t metric) { return metric == 1 || metric == 2 || metric == 3; }
+static int valid_metric(int32_t metric) { return metric >= 1 && metric <= 4; }
 
 /* (da, ia) precedes (db, ib) in the (distance, id) order */
 static int pair_less(double da, int64_t ia, double db, int64_t ib) {
@@ -679,7 +682,10 @@ int oracle_uhnsw_query(const oracle_csr* ga, const oracle_csr* gb, int32_t ma, i
     for (int32_t j = 0; j < k; ++j) {
       out_ids[j] = C[j];
       out_dist[j] = C[j] < 0 ? INFINITY
-                             : metric == 1 ? Cd[j] : metric == 2 ? sqrt(Cd[j]) : Cd[j] * Cd[j];
+                    : metric == 1 ? Cd[j]
+                    : metric == 2 ? sqrt(Cd[j])
+                    : metric == 3 ? Cd[j] * Cd[j]
+                                  : pow(Cd[j], 1.0 / 1.5);
     }
   } else {
     for (int32_t j = 0; j < tt; ++j) C32[j] = (int32_t)C[j];

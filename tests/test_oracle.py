@@ -441,3 +441,37 @@ def test_uhnsw_e_routing_cutoff(mixture_e):
     assert (lo >= 0).all()
     assert hi.tolist() == [7, -1, -1, -1, -1]
     assert one.tolist() == [7, -1, -1, -1, -1]     # p = 1 is the second graph's own metric
+
+
+# ----------------------------------------------------------------- fixed-p HNSW at p = 1.5 (Section 4.3)
+def test_base_dist_l15_pins():
+    """Metric 4 is sum |d_j|^(3/2): a hand value, and scipy's Minkowski p = 1.5
+    distance raised to 1.5."""
+    x = np.array([0.0, 4.0, 9.0, 2.5], np.float32)
+    q = np.array([1.0, 0.0, 0.0, 2.5], np.float32)
+    assert oracle.base_dist(x, q, 4) == 1.0 + 8.0 + 27.0 + 0.0
+    r = rng(12)
+    X = r.normal(size=(20, 24)).astype(np.float32)
+    Q = r.normal(size=(3, 24)).astype(np.float32)
+    D = cdist(Q.astype(np.float64), X.astype(np.float64), "minkowski", p=1.5)
+    for i in range(3):
+        got = [oracle.base_dist(X[j], Q[i], 4) for j in range(20)]
+        np.testing.assert_allclose(got, D[i] ** 1.5, rtol=1e-12)
+
+
+def test_l15_graph_direct_queries_are_exact_at_full_beam():
+    """A graph built under L1.5 answers p = 1.5 directly (no verification):
+    with ef = N the answer is the exact L1.5 top-K, distances S^(1/1.5)."""
+    w = I.WORKLOADS["mixture10k"].scaled(n=1500, nq=4)
+    base = I.base_vectors(w)
+    qs = I.query_vectors(w)
+    g15 = oracle.hnsw_build(base, 4, w.M, w.ef_construction, I.graph_levels(w, 2))
+    g2 = oracle.hnsw_build(base, 2, w.M, w.ef_construction, I.graph_levels(w, 2))
+    n = len(base)
+    D = cdist(qs.astype(np.float64), base.astype(np.float64), "minkowski", p=1.5)
+    ids, dist, st = oracle.uhnsw_batch(g15, g2, base, qs, 1.5, 10, n, metrics=(4, 2))
+    for i in range(len(qs)):
+        order = np.lexsort((np.arange(n), D[i]))[:10]
+        np.testing.assert_array_equal(ids[i], order)
+        np.testing.assert_allclose(dist[i], D[i, order], rtol=1e-12)
+    assert (st[:, 1] == 0).all()
