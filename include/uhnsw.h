@@ -89,7 +89,8 @@ typedef struct {
 typedef enum {
   UHNSW_BASE_L1 = 1,   /* sum |d_j|,       p = 1   */
   UHNSW_BASE_L2 = 2,   /* sum d_j^2,       p = 2   */
-  UHNSW_BASE_L05 = 3   /* sum |d_j|^(1/2), p = 0.5 */
+  UHNSW_BASE_L05 = 3,  /* sum |d_j|^(1/2), p = 0.5 */
+  UHNSW_BASE_L15 = 4   /* sum |d_j|^(3/2), p = 1.5 (a fixed-p HNSW graph, Section 4.3) */
 } uhnsw_base_metric;
 
 typedef struct {
@@ -426,7 +427,7 @@ typedef struct uhnsw_built uhnsw_built;
  * Build one HNSW graph on the host.
  *   base      host n x d float32 row-major (read during the call only)
  *   metric    a uhnsw_base_metric: 1 = L1 (G1), 2 = squared L2 (G2), 3 = L0.5
- *             (G0.5 of U-HNSW-E)
+ *             (G0.5 of U-HNSW-E), 4 = L1.5
  *   M         links per inserted node; layer-0 lists hold up to 2M
  *   ef_construction   beam width of the insertion search
  *   levels    host [n] int32, the level of each node (drawn by the caller)

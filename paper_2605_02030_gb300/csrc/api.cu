@@ -231,7 +231,9 @@ GraphDev to_dev(const DevGraph& g) {
 constexpr int kBlock = 128;
 
 // The p of a base metric (uhnsw_base_metric).
-double base_metric_p(int32_t m) { return m == UHNSW_BASE_L1 ? 1.0 : m == UHNSW_BASE_L2 ? 2.0 : 0.5; }
+double base_metric_p(int32_t m) {
+  return m == UHNSW_BASE_L1 ? 1.0 : m == UHNSW_BASE_L2 ? 2.0 : m == UHNSW_BASE_L05 ? 0.5 : 1.5;
+}
 
 }  // namespace
 
@@ -253,7 +255,7 @@ extern "C" int uhnsw_load(const float* base, int64_t n, int32_t d, const uhnsw_g
   for (int i = 0; i < 2; ++i) {
     const int32_t m = opts ? opts->base_metric[i] : 0;
     if (m == 0) continue;
-    if (m != UHNSW_BASE_L1 && m != UHNSW_BASE_L2 && m != UHNSW_BASE_L05)
+    if (m < UHNSW_BASE_L1 || m > UHNSW_BASE_L15)
       return fail(UHNSW_EINVAL, "uhnsw_load: base_metric[%d]=%d is not a uhnsw_base_metric", i, m);
     gm[i] = m;
   }

@@ -1,5 +1,6 @@
 // HNSW construction on the GPU (the index construction behind Section 2.2's
-// graphs: G1 under L1, G2 under L2, G0.5 under the L0.5 sum of U-HNSW-E).
+// graphs: G1 under L1, G2 under L2, G0.5 under the L0.5 sum of U-HNSW-E, and
+// the L1.5 graph of a fixed-p comparison).
 //
 // The published HNSW insertion, applied to batches of nodes at once:
 //   - nodes are inserted in id order; node 0 is the first entry point;
@@ -73,7 +74,10 @@ __device__ __forceinline__ float team_dist(const float* __restrict__ a, const fl
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const float v = fabsf(t[e]);
-      acc += metric == UHNSW_BASE_L1 ? v : metric == UHNSW_BASE_L05 ? sqrtf(v) : v * v;
+      acc += metric == UHNSW_BASE_L1    ? v
+             : metric == UHNSW_BASE_L05 ? sqrtf(v)
+             : metric == UHNSW_BASE_L15 ? v * sqrtf(v)
+                                        : v * v;
     }
   }
   acc += __shfl_xor_sync(kFull, acc, 1);
@@ -395,8 +399,8 @@ extern "C" int uhnsw_build_graph_gpu(const float* base, int64_t n, int32_t d, in
   *out = nullptr;
   if (!base || !levels || n < 1 || n > INT32_MAX / 2 || d < 1 || d > UHNSW_MAX_DIM)
     return fail(UHNSW_EINVAL, "uhnsw_build_graph_gpu: bad base/levels/n/d");
-  if (metric != UHNSW_BASE_L1 && metric != UHNSW_BASE_L2 && metric != UHNSW_BASE_L05)
-    return fail(UHNSW_EINVAL, "uhnsw_build_graph_gpu: metric must be 1, 2 or 3");
+  if (metric < UHNSW_BASE_L1 || metric > UHNSW_BASE_L15)
+    return fail(UHNSW_EINVAL, "uhnsw_build_graph_gpu: metric must be 1, 2, 3 or 4");
   if (M < 2 || 2 * M > UHNSW_MAX_DEGREE || ef_construction < 1 || ef_construction > 512)
     return fail(UHNSW_EINVAL, "uhnsw_build_graph_gpu: need 2 <= M <= %d, 1 <= efc <= 512",
                 UHNSW_MAX_DEGREE / 2);

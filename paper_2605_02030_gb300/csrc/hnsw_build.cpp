@@ -56,7 +56,8 @@ inline v4f load4(const float* p) {
 }
 
 // Base metric in FP32: metric 1 -> sum |d_j|, metric 2 -> sum d_j^2,
-// metric 3 -> sum |d_j|^(1/2) (the L0.5 graph of U-HNSW-E, Section 4.6).
+// metric 3 -> sum |d_j|^(1/2) (the L0.5 graph of U-HNSW-E, Section 4.6),
+// metric 4 -> sum |d_j|^(3/2) (an L1.5 graph, Section 4.3's fixed-p HNSW).
 // Four independent 4-wide partial sums, then a fixed combination order; the
 // same for every call, so the build is reproducible on one machine.
 float base_distance(const float* a, const float* b, int32_t d, int32_t metric) {
@@ -73,15 +74,17 @@ float base_distance(const float* a, const float* b, int32_t d, int32_t metric) {
         s3[u] += std::fabs(x3[u]);
       }
     }
-  } else if (metric == 3) {
+  } else if (metric == 3 || metric == 4) {
     for (; j + 16 <= d; j += 16) {
       v4f x0 = load4(a + j) - load4(b + j), x1 = load4(a + j + 4) - load4(b + j + 4);
       v4f x2 = load4(a + j + 8) - load4(b + j + 8), x3 = load4(a + j + 12) - load4(b + j + 12);
       for (int u = 0; u < 4; ++u) {
-        s0[u] += std::sqrt(std::fabs(x0[u]));
-        s1[u] += std::sqrt(std::fabs(x1[u]));
-        s2[u] += std::sqrt(std::fabs(x2[u]));
-        s3[u] += std::sqrt(std::fabs(x3[u]));
+        const float a0 = std::fabs(x0[u]), a1 = std::fabs(x1[u]);
+        const float a2 = std::fabs(x2[u]), a3 = std::fabs(x3[u]);
+        s0[u] += metric == 3 ? std::sqrt(a0) : a0 * std::sqrt(a0);
+        s1[u] += metric == 3 ? std::sqrt(a1) : a1 * std::sqrt(a1);
+        s2[u] += metric == 3 ? std::sqrt(a2) : a2 * std::sqrt(a2);
+        s3[u] += metric == 3 ? std::sqrt(a3) : a3 * std::sqrt(a3);
       }
     }
   } else {
@@ -98,7 +101,8 @@ float base_distance(const float* a, const float* b, int32_t d, int32_t metric) {
   float r = (s[0] + s[1]) + (s[2] + s[3]);
   for (; j < d; ++j) {
     float x = a[j] - b[j];
-    r += metric == 1 ? std::fabs(x) : metric == 3 ? std::sqrt(std::fabs(x)) : x * x;
+    const float a = std::fabs(x);
+    r += metric == 1 ? a : metric == 3 ? std::sqrt(a) : metric == 4 ? a * std::sqrt(a) : x * x;
   }
   return r;
 }
@@ -289,8 +293,8 @@ extern "C" int uhnsw_build_graph(const float* base, int64_t n, int32_t d, int32_
   *out = nullptr;
   if (!base || !levels || n < 1 || n > INT32_MAX || d < 1 || d > UHNSW_MAX_DIM)
     return uhnsw_internal::fail(UHNSW_EINVAL, "uhnsw_build_graph: bad base/levels/n/d");
-  if (metric != 1 && metric != 2 && metric != 3)
-    return uhnsw_internal::fail(UHNSW_EINVAL, "uhnsw_build_graph: metric must be 1, 2 or 3");
+  if (metric < 1 || metric > 4)
+    return uhnsw_internal::fail(UHNSW_EINVAL, "uhnsw_build_graph: metric must be 1, 2, 3 or 4");
   if (M < 2 || 2 * M > UHNSW_MAX_DEGREE || ef_construction < 1)
     return uhnsw_internal::fail(UHNSW_EINVAL, "uhnsw_build_graph: need 2 <= M <= %d, efc >= 1",
                                 UHNSW_MAX_DEGREE / 2);

@@ -116,9 +116,10 @@ __device__ __forceinline__ float query_tau(const QueryArgs& a, int64_t qi) {
 
 // The distance a direct query returns: the base sum's root S^(1/p_base).
 __device__ __forceinline__ float base_root(int metric, float s) {
-  return metric == UHNSW_BASE_L1 ? s
-         : metric == UHNSW_BASE_L2 ? sqrtf(s)
-                                   : (float)((double)s * (double)s);
+  return metric == UHNSW_BASE_L1    ? s
+         : metric == UHNSW_BASE_L2  ? sqrtf(s)
+         : metric == UHNSW_BASE_L05 ? (float)((double)s * (double)s)
+                                    : (float)pow((double)s, 1.0 / 1.5);
 }
 
 // Dynamic shared-memory carve-up (byte offsets), identical on host and device.
@@ -249,6 +250,7 @@ __device__ __forceinline__ void dist_batch(const T* __restrict__ rows, int d_pad
           const float df = x[e] - qv[c][e];
           if (METRIC == UHNSW_BASE_L1) acc += fabsf(df);
           else if (METRIC == UHNSW_BASE_L05) acc += hw_sqrt(fabsf(df));
+          else if (METRIC == UHNSW_BASE_L15) acc += fabsf(df) * hw_sqrt(fabsf(df));
           else acc = fmaf(df, df, acc);
         }
       }
@@ -267,7 +269,8 @@ __device__ __forceinline__ void dist_batch_metric(int metric, const T* rows, int
                                                   int64_t n, int32_t* err) {
   if (metric == UHNSW_BASE_L1) dist_batch<T, TEAM, CPL, BLOCK, 1>(rows, d_pad, qv, ids, out, m, n, err);
   else if (metric == UHNSW_BASE_L2) dist_batch<T, TEAM, CPL, BLOCK, 2>(rows, d_pad, qv, ids, out, m, n, err);
-  else dist_batch<T, TEAM, CPL, BLOCK, 3>(rows, d_pad, qv, ids, out, m, n, err);
+  else if (metric == UHNSW_BASE_L05) dist_batch<T, TEAM, CPL, BLOCK, 3>(rows, d_pad, qv, ids, out, m, n, err);
+  else dist_batch<T, TEAM, CPL, BLOCK, 4>(rows, d_pad, qv, ids, out, m, n, err);
 }
 
 // ---------------------------------------------------------------- verification

@@ -116,8 +116,8 @@ __device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
   return r;
 }
 
-// Elementwise |x - q| (metric 1), (x - q)^2 (metric 2) or |x - q|^(1/2)
-// (metric 3) summed over
+// Elementwise |x - q| (metric 1), (x - q)^2 (metric 2), |x - q|^(1/2)
+// (metric 3) or |x - q|^(3/2) (metric 4) summed over
 // one 16-byte chunk of a row, as even / odd element pairs accumulated into acc.
 // q holds the chunk's query values as FP32 pairs (little-endian: element 2e in
 // the low half).
@@ -136,6 +136,12 @@ __device__ __forceinline__ void chunk_partial(const uint4& v, const uint64_t (&q
       float lo, hi;
       asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(df));
       acc = f2_add(acc, f2_pack(hw_sqrt(fabsf(lo)), hw_sqrt(fabsf(hi))));
+    } else if (METRIC == UHNSW_BASE_L15) {
+      float lo, hi;
+      asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(df));
+      lo = fabsf(lo);
+      hi = fabsf(hi);
+      acc = f2_add(acc, f2_pack(lo * hw_sqrt(lo), hi * hw_sqrt(hi)));
     } else {
       acc = f2_fma(df, df, acc);
     }
@@ -257,7 +263,8 @@ __device__ __forceinline__ void warp_dist_metric(int metric, const T* rows, int 
                                                  int m, int64_t n, int32_t* err) {
   if (metric == UHNSW_BASE_L1) warp_dist<T, TEAM, CPL, U, 1>(rows, d_pad, qs, ids, out, m, n, err);
   else if (metric == UHNSW_BASE_L2) warp_dist<T, TEAM, CPL, U, 2>(rows, d_pad, qs, ids, out, m, n, err);
-  else warp_dist<T, TEAM, CPL, U, 3>(rows, d_pad, qs, ids, out, m, n, err);
+  else if (metric == UHNSW_BASE_L05) warp_dist<T, TEAM, CPL, U, 3>(rows, d_pad, qs, ids, out, m, n, err);
+  else warp_dist<T, TEAM, CPL, U, 4>(rows, d_pad, qs, ids, out, m, n, err);
 }
 
 // Drops the candidates that cannot enter a full W (those not before its last

@@ -48,8 +48,9 @@ class _LoadOpts(C.Structure):
                 ("reserved", C.c_int32 * 5)]
 
 
-# Base metrics (uhnsw_base_metric): 1 = L1, 2 = squared L2, 3 = L0.5 sum.
-BASE_L1, BASE_L2, BASE_L05 = 1, 2, 3
+# Base metrics (uhnsw_base_metric): 1 = L1, 2 = squared L2, 3 = L0.5 sum,
+# 4 = L1.5 sum.
+BASE_L1, BASE_L2, BASE_L05, BASE_L15 = 1, 2, 3, 4
 U_HNSW = (BASE_L1, BASE_L2)        # G1 and G2, cutoff 1.4
 U_HNSW_E = (BASE_L05, BASE_L1)     # G0.5 and G1, cutoff 0.6 (Section 4.6)
 

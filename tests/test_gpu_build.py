@@ -107,7 +107,7 @@ def test_gpu_build_validation(U):
     base = np.zeros((10, 4), np.float32)
     lv = np.zeros(10, np.int32)
     with pytest.raises(U.UHNSWError):
-        U.build_graph(base, 4, 4, 10, lv, device="gpu")
+        U.build_graph(base, 5, 4, 10, lv, device="gpu")
     with pytest.raises(U.UHNSWError):
         U.build_graph(base, 1, 4, 600, lv, device="gpu")       # efConstruction above 512
     lv[3] = -1

@@ -78,7 +78,7 @@ def test_build_graph_validation(lib):
     base = np.zeros((10, 4), np.float32)
     lv = np.zeros(10, np.int32)
     h = C.c_void_p(0)
-    assert lib.uhnsw_build_graph(base.ctypes.data, 10, 4, 4, 4, 10, lv.ctypes.data, 1, C.byref(h)) == -1
+    assert lib.uhnsw_build_graph(base.ctypes.data, 10, 4, 5, 4, 10, lv.ctypes.data, 1, C.byref(h)) == -1
     assert lib.uhnsw_build_graph(base.ctypes.data, 10, 4, 0, 4, 10, lv.ctypes.data, 1, C.byref(h)) == -1
     assert lib.uhnsw_build_graph(base.ctypes.data, 10, 4, 1, 1, 10, lv.ctypes.data, 1, C.byref(h)) == -1
     lv[3] = -2
