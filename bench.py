@@ -778,6 +778,67 @@ def run_idealized(args, log):
     idx.close()
 
 
+# ---------------------------------------------------------------- fixed-p HNSW
+def run_fixed_p(args, log):
+    """Section 4.3's comparison on the sift1m recipe, at the two p where the
+    paper finds plain HNSW faster (0.5 and 1.5): U-HNSW (G1, G2, verification)
+    against an HNSW graph built under the query's own L_p and searched
+    directly, each at the smallest beam that reaches recall@10 >= 0.95."""
+    import torch
+    import paper_2605_02030_gb300 as pkg
+    from paper_2605_02030_gb300 import uhnsw as U
+
+    pkg.build()
+    w = workload(args)
+    base = I.base_vectors(w)
+    qs = I.query_vectors(w)
+    g1, g2 = graphs_for(w, base, log)
+    q_dev = torch.from_numpy(qs).cuda()
+    flush = torch.empty(384 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    k = 10
+
+    def measure(idx, p_dev, gt):
+        best = None
+        for ef in EF_SWEEP:
+            ids, _, _ = idx.search(q_dev, p_dev, k=k, ef=ef, persistent=True)
+            torch.cuda.synchronize()
+            hits = _recall_at_k(ids.cpu().numpy(), gt, np.full(w.nq, k))
+            best = (ef, float(hits.mean()))
+            if best[1] >= RECALL_TARGET:
+                break
+        ms = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(1.0)
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            idx.search(q_dev, p_dev, k=k, ef=best[0], persistent=True, use_graph=True)
+            e.record()
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                ms.append(a.elapsed_time(e))
+        return {"ef": best[0], "recall_at_10": round(best[1], 4),
+                "qps": round(w.nq / statistics.mean(ms) * 1e3, 1)}
+
+    rows = {}
+    uh = U.Index(base, g1, g2, traverse_dtype="f16")
+    for pv, metric, other in ((0.5, U.BASE_L05, (g1, U.BASE_L1)), (1.5, U.BASE_L15, (g2, U.BASE_L2))):
+        p_dev = torch.full((w.nq,), pv, dtype=torch.float32, device="cuda")
+        gt = uh.exact(q_dev, p_dev, k)[0].cpu().numpy()
+        t0 = time.time()
+        gp = U.build_graph(base, metric, w.M, w.ef_construction, I.graph_levels(w, 2), device="gpu")
+        log(f"built the p={pv} graph on the GPU in {time.time() - t0:.1f} s")
+        fixed = U.Index(base, gp, other[0], traverse_dtype="f16", metrics=(metric, other[1]))
+        rows[str(pv)] = {"u_hnsw": measure(uh, p_dev, gt), "fixed_p_hnsw": measure(fixed, p_dev, gt)}
+        log(f"p={pv}: {rows[str(pv)]}")
+        fixed.close()
+    uh.close()
+    print(json.dumps({"metric": "QPS at recall@10>=0.95: U-HNSW vs HNSW built under the query's "
+                                "own L_p (Section 4.3)",
+                      "config": {"workload": f"sift1m: N={w.n:,} d={w.d}, {w.nq:,} queries, "
+                                             "every query at the same p; FP16 batched form",
+                                 "results": rows}}), flush=True)
+
+
 # ---------------------------------------------------------------- oracle arm
 def cpu_baseline(w, base, qs, p, g1, g2, ef, k, seconds):
     """The oracle (single-threaded FP64 Algorithm 1) on a time-bounded sample of
@@ -867,6 +928,8 @@ def main():
                     help="Section 3.2's idealized-recall experiment and a recall-targeted t per p")
     ap.add_argument("--target", type=float, default=0.97,
                     help="--idealized: idealized-recall target of the t plan")
+    ap.add_argument("--fixed-p", action="store_true",
+                    help="Section 4.3's comparison with HNSW built under the query's own L_p")
     ap.add_argument("--quiet", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -879,6 +942,8 @@ def main():
         run_reference(args, log)
     elif args.idealized:
         run_idealized(args, log)
+    elif args.fixed_p:
+        run_fixed_p(args, log)
     elif args.workload != "sift1m":
         run_workload(args, log)
     else:
