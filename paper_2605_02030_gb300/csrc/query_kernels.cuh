@@ -128,13 +128,17 @@ struct SmemLayout {
   __host__ __device__ SmemLayout(int d_pad, int ef_cap, int hash_bits, int cmax, int k_max,
                                  int vcap, int stage_bytes = 0) {
     int o = 0;
-    stage = o; o += align16(stage_bytes);
     qs = o; o += align16(d_pad * 4);
     bd0 = o; o += align16(ef_cap * 4);
     bi0 = o; o += align16(ef_cap * 4);
     bd1 = o; o += align16(ef_cap * 4);
     bi1 = o; o += align16(ef_cap * 4);
-    hash = o; o += align16((hash_bits > 0 ? (1 << hash_bits) : 0) * 4);
+    // The visited table lives during the search, the staged verification rows
+    // after it: they share one region.
+    const int hash_bytes = align16((hash_bits > 0 ? (1 << hash_bits) : 0) * 4);
+    hash = o;
+    stage = o;
+    o += hash_bytes > align16(stage_bytes) ? hash_bytes : align16(stage_bytes);
     cd = o; o += align16(cmax * 4);
     ci = o; o += align16(cmax * 4);
     sd = o; o += align16(cmax * 4);

@@ -426,9 +426,10 @@ def test_large_beam_buckets_fall_back_to_the_block_kernel(U):
     g1, g2 = oracle_graphs("mixture10k", 3000, 40, 1 / 16)
     idx = U.Index(base, g1, g2, traverse_dtype="f32")
     ef = np.where(np.arange(len(qs)) % 2 == 0, 32, 500).astype(np.int32)
-    # 256 staged rows: the ef <= 64 bucket fits four warp queries per block
-    # (141 KB), the ef 512 bucket does not (233 KB > 227 KB)
-    kw = dict(k=10, ef=dev(ef), k_max=10, ef_max=512, stage_bytes=32768)
+    # 384 staged rows (48 KB per query, sharing its region with the visited
+    # table): the ef <= 64 bucket fits four warp queries per block (204 KB),
+    # the ef 512 bucket does not (232,704 B > 227 KB)
+    kw = dict(k=10, ef=dev(ef), k_max=10, ef_max=512, stage_bytes=49152)
     a = idx.search(dev(qs), dev(p), persistent=True, **kw)
     b = idx.search(dev(qs), dev(p), query_threads=128, **kw)
     torch.cuda.synchronize()
