@@ -693,10 +693,24 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
 
 // WARPS independent queries per block; a.queue_head set = persistent (each
 // warp pulls the next query index), else query = blockIdx.x * WARPS + warp.
-#ifndef UHNSW_WARP_MINB
-#define UHNSW_WARP_MINB 8
+//
+// Blocks per SM asked of the register allocator: 7 for FP16/BF16 rows
+// (72 registers, 28 queries per SM), 6 for FP32 rows (85 registers).  These
+// measured faster than 8 blocks at 64 registers (1.89 vs 1.99 ms and 2.45 vs
+// 2.74 ms per 10,000 queries on 1M x 128): no spills, and a smaller
+// shared-memory carve-out leaves a larger L1 for the rows.
+#ifdef UHNSW_WARP_MINB
+template <typename T>
+struct WarpMinBlocks {
+  static constexpr int value = UHNSW_WARP_MINB;
+};
+#else
+template <typename T>
+struct WarpMinBlocks {
+  static constexpr int value = sizeof(T) == 4 ? 6 : 7;
+};
 #endif
-template <typename T, int TEAM, int CPL, int U, int WARPS, int MINB = UHNSW_WARP_MINB>
+template <typename T, int TEAM, int CPL, int U, int WARPS, int MINB = WarpMinBlocks<T>::value>
 __global__ void __launch_bounds__(WARPS * 32, MINB) uhnsw_wsearch_kernel(const QueryArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLayout L(a.d_pad, a.ef_cap, a.hash_bits, a.cmax, a.k_max, 0, a.stage_bytes);
