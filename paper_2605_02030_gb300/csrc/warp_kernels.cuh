@@ -694,11 +694,12 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
 // WARPS independent queries per block; a.queue_head set = persistent (each
 // warp pulls the next query index), else query = blockIdx.x * WARPS + warp.
 //
-// Blocks per SM asked of the register allocator: 7 for FP16/BF16 rows
-// (72 registers, 28 queries per SM), 6 for FP32 rows (85 registers).  These
-// measured faster than 8 blocks at 64 registers (1.89 vs 1.99 ms and 2.45 vs
-// 2.74 ms per 10,000 queries on 1M x 128): no spills, and a smaller
-// shared-memory carve-out leaves a larger L1 for the rows.
+// Blocks per SM asked of the register allocator: 6 (up to 85 registers, 24
+// queries per SM).  With the default shapes (FP16/BF16: 8 lanes x 2 chunks x
+// 3 rows per team; FP32: 16 x 2 x 3) this is free of spills, and it measured
+// faster than 8 blocks at 64 registers, whose spill traffic reached DRAM
+// (1.83 vs 1.99 ms and 2.44 vs 2.74 ms per 10,000 queries on 1M x 128).  The
+// smaller shared-memory carve-out also leaves a larger L1 for the rows.
 #ifdef UHNSW_WARP_MINB
 template <typename T>
 struct WarpMinBlocks {
@@ -707,7 +708,7 @@ struct WarpMinBlocks {
 #else
 template <typename T>
 struct WarpMinBlocks {
-  static constexpr int value = sizeof(T) == 4 ? 6 : 7;
+  static constexpr int value = 6;
 };
 #endif
 template <typename T, int TEAM, int CPL, int U, int WARPS, int MINB = WarpMinBlocks<T>::value>

@@ -34,6 +34,7 @@ int wocc_one(size_t smem) {
     switch (key_) {                                                          \
       case 8014: return CALL(T, 8, 1, 4);                                    \
       case 8022: return CALL(T, 8, 2, 2);                                    \
+      case 8023: return CALL(T, 8, 2, 3);                                    \
       case 16022: return CALL(T, 16, 2, 2);                                  \
       case 16023: return CALL(T, 16, 2, 3);                                  \
       case 32022: return CALL(T, 32, 2, 2);                                  \
