@@ -157,7 +157,7 @@ cudaError_t launch_bucketing(const QueryArgs& a, const BeamBuckets& bb, int32_t*
 bool pick_warp_shape(uhnsw_dtype dt, int chunks, int team_pref, WarpShape* out) {
   // shapes free of spills at 6 blocks per SM; the first covering shape of
   // each list measured fastest for 128-dimension rows (1M x 128, ef 48)
-  static const WarpShape f32[] = {{8, 1, 4},  {8, 2, 2},  {16, 2, 3}, {32, 2, 2},
+  static const WarpShape f32[] = {{8, 1, 4},  {8, 2, 2},  {16, 2, 4}, {32, 2, 2},
                                   {32, 4, 2}, {32, 8, 1}, {32, 16, 1}};
   static const WarpShape f16[] = {{8, 1, 4},  {8, 2, 3},  {16, 2, 2}, {32, 2, 2},
                                   {32, 4, 2}, {32, 8, 1}, {32, 16, 1}};

@@ -36,7 +36,7 @@ int wocc_one(size_t smem) {
       case 8022: return CALL(T, 8, 2, 2);                                    \
       case 8023: return CALL(T, 8, 2, 3);                                    \
       case 16022: return CALL(T, 16, 2, 2);                                  \
-      case 16023: return CALL(T, 16, 2, 3);                                  \
+      case 16024: return CALL(T, 16, 2, 4);                                  \
       case 32022: return CALL(T, 32, 2, 2);                                  \
       case 32042: return CALL(T, 32, 4, 2);                                  \
       case 32081: return CALL(T, 32, 8, 1);                                  \
