@@ -846,6 +846,62 @@ def run_fixed_p(args, log):
                                  "results": rows}}), flush=True)
 
 
+# ---------------------------------------------------------------- verification
+def run_verify(args, log):
+    """The L_p verification kernel alone (Algorithm 1, lines 6-10, exact mode
+    with the partial-sum drop) on the sift1m recipe: each query's candidate
+    set is its exact L1 top-256 (what candidate generation approximates),
+    p = 0.7 for every query (two SFU operations per term), K = 50.  Reports
+    the SFU operations per second against the nominal SFU rate."""
+    import torch
+    import paper_2605_02030_gb300 as pkg
+    from paper_2605_02030_gb300 import uhnsw as U
+
+    pkg.build()
+    w = workload(args)
+    base = I.base_vectors(w)
+    qs = I.query_vectors(w)
+    g1, g2 = graphs_for(w, base, log)
+    idx = U.Index(base, g1, g2)
+    q_dev = torch.from_numpy(qs).cuda()
+    t, K = 256, 50
+    cand = idx.exact(q_dev, torch.ones(w.nq, device="cuda"), t)[0].to(torch.int32).contiguous()
+    p_dev = torch.full((w.nq,), 0.7, dtype=torch.float32, device="cuda")
+    flush = torch.empty(384 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ms = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        idx.verify(q_dev, p_dev, cand, K)
+        e.record()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            ms.append(a.elapsed_time(e))
+    _, _, st = idx.verify(q_dev, p_dev, cand, K, stats=True)
+    st = st.cpu().numpy().astype(np.int64)
+    terms = int(st[:, 2].sum())
+    mean_ms = statistics.mean(ms)
+    sfu_ops = 2 * terms                      # lg2 and ex2 per term
+    # nominal SFU rate: 16 lg2 / ex2 results per SM per clock
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 16 * 2.07e9
+    line = {"metric": "L_p verification alone: SFU operations per second (p = 0.7, t = 256, K = 50)",
+            "value": round(sfu_ops / (mean_ms / 1e3) / 1e12, 4), "unit": "T SFU ops/s",
+            "ms_per_launch": round(mean_ms, 4),
+            "roofline": {"bound": "alu", "achieved": round(sfu_ops / (mean_ms / 1e3) / 1e12, 4),
+                         "peak": round(peak / 1e12, 3), "unit": "T SFU ops/s",
+                         "frac": round(sfu_ops / (mean_ms / 1e3) / peak, 4),
+                         "peak_source": f"nominal: {sms} SMs x 16 lg2/ex2 per clock x 2.07 GHz"},
+            "config": {"workload": f"sift1m: N={w.n:,} d={w.d}, {w.nq:,} queries, candidates = "
+                                   "exact L1 top-256 of each query",
+                       "terms_per_query": round(terms / w.nq, 1),
+                       "terms_without_drop_per_query": t * w.d,
+                       "candidates_started_per_query": float(st[:, 1].mean())}}
+    print(json.dumps(line), flush=True)
+    idx.close()
+
+
 # ---------------------------------------------------------------- oracle arm
 def cpu_baseline(w, base, qs, p, g1, g2, ef, k, seconds):
     """The oracle (single-threaded FP64 Algorithm 1) on a time-bounded sample of
@@ -937,6 +993,8 @@ def main():
                     help="--idealized: idealized-recall target of the t plan")
     ap.add_argument("--fixed-p", action="store_true",
                     help="Section 4.3's comparison with HNSW built under the query's own L_p")
+    ap.add_argument("--verify-roofline", action="store_true",
+                    help="the L_p verification kernel alone, against the SFU rate")
     ap.add_argument("--quiet", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -951,6 +1009,8 @@ def main():
         run_idealized(args, log)
     elif args.fixed_p:
         run_fixed_p(args, log)
+    elif args.verify_roofline:
+        run_verify(args, log)
     elif args.workload != "sift1m":
         run_workload(args, log)
     else:
