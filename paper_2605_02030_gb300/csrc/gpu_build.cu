@@ -383,12 +383,6 @@ int reverse_smem(int d_pad, int M0) {
 }  // namespace
 }  // namespace uhnsw_dev
 
-namespace uhnsw_internal {
-uhnsw_built* make_built(int64_t n, int32_t M, int32_t M0, const int32_t* levels, int32_t entry,
-                        int32_t top, const int32_t* ell0, const int32_t* up_off,
-                        const int32_t* up_adj);
-}
-
 extern "C" int uhnsw_build_graph_gpu(const float* base, int64_t n, int32_t d, int32_t metric,
                                      int32_t M, int32_t ef_construction, const int32_t* levels,
                                      uhnsw_built** out) {

@@ -376,9 +376,7 @@ extern "C" int uhnsw_build_graph(const float* base, int64_t n, int32_t d, int32_
 }
 
 namespace uhnsw_internal {
-// CSR graph from padded adjacency tables (layer 0 [n][M0], upper rows [rows][M]
-// with the row of (v, l) at up_off[v] + l - 1; -1 after the last link), as the
-// GPU builder leaves them.
+// CSR graph from the padded adjacency tables the GPU builder leaves.
 uhnsw_built* make_built(int64_t n, int32_t M, int32_t M0, const int32_t* levels, int32_t entry,
                         int32_t top, const int32_t* ell0, const int32_t* up_off,
                         const int32_t* up_adj) {

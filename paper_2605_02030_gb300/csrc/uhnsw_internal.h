@@ -17,4 +17,11 @@ int fail(int code, const char* fmt, ...);
 int64_t query_state_bytes(const uhnsw_index* idx, int32_t ef, int32_t k,
                           const uhnsw_search_opts* opts);
 
+// A built graph (CSR per level) from padded adjacency tables: layer 0
+// [n][M0], upper rows [rows][M] with the row of (v, l) at up_off[v] + l - 1,
+// -1 after the last link.  nullptr when host memory runs out.
+uhnsw_built* make_built(int64_t n, int32_t M, int32_t M0, const int32_t* levels, int32_t entry,
+                        int32_t top, const int32_t* ell0, const int32_t* up_off,
+                        const int32_t* up_adj);
+
 }  // namespace uhnsw_internal
