@@ -67,6 +67,9 @@ def _load():
     lib.oracle_hnsw_build.restype = P
     lib.oracle_hnsw_build.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                       C.c_int32, P, P]
+    lib.oracle_hnsw_build_p.restype = P
+    lib.oracle_hnsw_build_p.argtypes = [P, C.c_int64, C.c_int32, C.c_double, C.c_int32, C.c_int32,
+                                        C.c_int32, P, P]
     lib.oracle_graph_free.argtypes = [P]
     lib.oracle_graph_num_levels.restype = C.c_int32
     lib.oracle_graph_num_levels.argtypes = [P]
@@ -77,6 +80,9 @@ def _load():
     lib.oracle_hnsw_search.restype = C.c_int
     lib.oracle_hnsw_search.argtypes = [C.POINTER(_CSR), P, C.c_int32, C.c_int32, P, C.c_int32,
                                        C.c_int32, P, P, P]
+    lib.oracle_hnsw_search_p.restype = C.c_int
+    lib.oracle_hnsw_search_p.argtypes = [C.POINTER(_CSR), P, C.c_int32, C.c_double, P, C.c_int32,
+                                         C.c_int32, P, P, P]
     lib.oracle_verify_exact.restype = C.c_int
     lib.oracle_verify_exact.argtypes = [P, C.c_int32, P, C.c_double, P, C.c_int32, C.c_int32,
                                         C.c_int32, P, P, P]
@@ -87,6 +93,11 @@ def _load():
     lib.oracle_uhnsw_query.argtypes = [C.POINTER(_CSR), C.POINTER(_CSR), C.c_int32, C.c_int32, P,
                                        C.c_int32, P, C.c_float, C.c_int32, C.c_int32, C.c_int32,
                                        C.c_float, C.c_int32, C.c_float, C.c_int32, P, P, P]
+    lib.oracle_uhnsw_query_p.restype = C.c_int
+    lib.oracle_uhnsw_query_p.argtypes = [C.POINTER(_CSR), C.POINTER(_CSR), C.c_double, C.c_double,
+                                         P, C.c_int32, P, C.c_float, C.c_int32, C.c_int32,
+                                         C.c_int32, C.c_float, C.c_int32, C.c_float, C.c_int32, P,
+                                         P, P]
     _lib = lib
     return lib
 
@@ -111,6 +122,16 @@ def lp_sum(x, q, p: float) -> float:
 # its root, sum |d_j|^(3/2).  METRIC_P is the p of each.  U-HNSW uses G1 (L1) and G2 (L2) with cutoff 1.4; U-HNSW-E
 # (Section 4.6) uses G0.5 (L0.5) and G1 (L1) with cutoff 0.6.
 METRIC_P = {1: 1.0, 2: 2.0, 3: 0.5, 4: 1.5}
+
+
+def _bp(p) -> float:
+    """A graph's base p as the FP32 value it is stored as, widened to FP64:
+    a graph built under L_bp uses S_bp = sum |d_j|^bp (the fixed-p HNSW of
+    Section 4.3, one graph per p)."""
+    bp = float(np.float32(p))
+    if not 0.0 < bp <= 2.0:
+        raise ValueError(f"base p {p} outside (0, 2]")
+    return bp
 
 
 def base_dist(x, q, metric: int) -> float:
@@ -148,8 +169,10 @@ def select_heuristic(base, cand, cand_d, m: int, metric: int):
     return out[:r].copy()
 
 
-def hnsw_build(base, metric: int, M: int, ef_construction: int, levels, M0: int | None = None):
-    """HNSW graph under L1 (metric=1), L2 (2), L0.5 (3) or L1.5 (4), as a CSR dict:
+def hnsw_build(base, metric: int | None, M: int, ef_construction: int, levels,
+               M0: int | None = None, base_p: float | None = None):
+    """HNSW graph under L1 (metric=1), L2 (2), L0.5 (3) or L1.5 (4), or, with
+    metric None and base_p given, under L_base_p, as a CSR dict:
     {num_levels, entry_point, max_degree0, max_degree, n,
      levels: [{nodes int32, offsets int64, nbrs int32}, ...]} (level 0 nodes = all ids)."""
     base = _f32(base)
@@ -158,8 +181,12 @@ def hnsw_build(base, metric: int, M: int, ef_construction: int, levels, M0: int 
     M0 = 2 * M if M0 is None else M0
     lib = _load()
     st = C.c_int32(0)
-    g = lib.oracle_hnsw_build(_ptr(base), n, d, metric, M, M0, ef_construction, _ptr(levels),
-                              C.byref(st))
+    if metric is None:
+        g = lib.oracle_hnsw_build_p(_ptr(base), n, d, _bp(base_p), M, M0, ef_construction,
+                                    _ptr(levels), C.byref(st))
+    else:
+        g = lib.oracle_hnsw_build(_ptr(base), n, d, metric, M, M0, ef_construction, _ptr(levels),
+                                  C.byref(st))
     if not g:
         raise ValueError(f"oracle_hnsw_build: status {st.value}")
     try:
@@ -207,16 +234,21 @@ class _CSRHolder:
 
 
 # ---------------------------------------------------------------- O3
-def hnsw_search(graph, base, q, metric: int, ef: int, t: int):
-    """KnnSearch(q, t) with beam ef on a CSR graph: (ids int64 [t], base dist
-    float64 [t], number of base-distance evaluations)."""
+def hnsw_search(graph, base, q, metric: int | None, ef: int, t: int, base_p: float | None = None):
+    """KnnSearch(q, t) with beam ef on a CSR graph (base metric by code, or
+    L_base_p when metric is None): (ids int64 [t], base dist float64 [t],
+    number of base-distance evaluations)."""
     base, q = _f32(base), _f32(q)
     h = _CSRHolder(graph)
     ids = np.empty(t, np.int64)
     dd = np.empty(t, np.float64)
     nd = C.c_int64(0)
-    rc = _load().oracle_hnsw_search(C.byref(h.s), _ptr(base), base.shape[1], metric, _ptr(q), ef, t,
-                                    _ptr(ids), _ptr(dd), C.byref(nd))
+    if metric is None:
+        rc = _load().oracle_hnsw_search_p(C.byref(h.s), _ptr(base), base.shape[1], _bp(base_p),
+                                          _ptr(q), ef, t, _ptr(ids), _ptr(dd), C.byref(nd))
+    else:
+        rc = _load().oracle_hnsw_search(C.byref(h.s), _ptr(base), base.shape[1], metric, _ptr(q),
+                                        ef, t, _ptr(ids), _ptr(dd), C.byref(nd))
     if rc != 0:
         raise ValueError(f"oracle_hnsw_search: {rc}")
     return ids, dd, nd.value
@@ -255,27 +287,36 @@ def verify_paper(base, q, p: float, cand, k: int, kappa: int, tau: float):
 
 # ---------------------------------------------------------------- Algorithm 1
 def uhnsw_query(g1, g2, base, q, p: float, k: int, ef: int, t: int = 0, tau: float = 0.92,
-                kappa: int = 0, cutoff: float = 1.4, mode: int = 0, metrics=(1, 2), _holders=None):
+                kappa: int = 0, cutoff: float = 1.4, mode: int = 0, metrics=(1, 2), _holders=None,
+                base_p=None):
     """One query of Algorithm 1: (ids int64 [k], dist float64 [k], stats [N_b, N_p, terms]).
     g1 / g2 are the graphs routed for p <= cutoff / p > cutoff, under the base
-    metrics `metrics` (U-HNSW: (1, 2); U-HNSW-E: (3, 1) with cutoff 0.6)."""
+    metrics `metrics` (U-HNSW: (1, 2); U-HNSW-E: (3, 1) with cutoff 0.6), or,
+    when base_p = (pa, pb) is given, under L_pa and L_pb (a fixed HNSW at p:
+    the same L_p graph in both slots, base_p = (p, p))."""
     base, q = _f32(base), _f32(q)
     h1 = _holders[0] if _holders else _CSRHolder(g1)
     h2 = _holders[1] if _holders else _CSRHolder(g2)
     ids = np.empty(k, np.int64)
     dist = np.empty(k, np.float64)
     st = np.zeros(3, np.int64)
-    rc = _load().oracle_uhnsw_query(C.byref(h1.s), C.byref(h2.s), int(metrics[0]), int(metrics[1]),
-                                    _ptr(base), base.shape[1], _ptr(q), float(p), k, ef, t,
-                                    float(tau), kappa, float(cutoff), mode, _ptr(ids), _ptr(dist),
-                                    _ptr(st))
+    if base_p is not None:
+        rc = _load().oracle_uhnsw_query_p(C.byref(h1.s), C.byref(h2.s), _bp(base_p[0]),
+                                          _bp(base_p[1]), _ptr(base), base.shape[1], _ptr(q),
+                                          float(p), k, ef, t, float(tau), kappa, float(cutoff),
+                                          mode, _ptr(ids), _ptr(dist), _ptr(st))
+    else:
+        rc = _load().oracle_uhnsw_query(C.byref(h1.s), C.byref(h2.s), int(metrics[0]),
+                                        int(metrics[1]), _ptr(base), base.shape[1], _ptr(q),
+                                        float(p), k, ef, t, float(tau), kappa, float(cutoff), mode,
+                                        _ptr(ids), _ptr(dist), _ptr(st))
     if rc != 0:
         raise ValueError(f"oracle_uhnsw_query: {rc}")
     return ids, dist, st
 
 
 def uhnsw_batch(g1, g2, base, queries, p, k, ef, t=0, tau=0.92, kappa=0, cutoff=1.4, mode=0,
-                metrics=(1, 2)):
+                metrics=(1, 2), base_p=None):
     """Algorithm 1 over a batch (per-query p, k, ef arrays or scalars).
     Returns ids int64 [nq, kmax] and dist float64 [nq, kmax] (-1 / inf padded)."""
     queries = _f32(queries)
@@ -290,7 +331,7 @@ def uhnsw_batch(g1, g2, base, queries, p, k, ef, t=0, tau=0.92, kappa=0, cutoff=
     stats = np.zeros((nq, 3), np.int64)
     for i in range(nq):
         a, b, s = uhnsw_query(g1, g2, base, queries[i], float(p[i]), int(k[i]), int(ef[i]), t, tau,
-                              kappa, cutoff, mode, metrics, _holders=holders)
+                              kappa, cutoff, mode, metrics, _holders=holders, base_p=base_p)
         ids[i, :k[i]] = a
         dist[i, :k[i]] = b
         stats[i] = s

@@ -19,9 +19,12 @@
  *                         Malkov & Yashunin, Algorithms 1, 2 and 4).
  *                         PARITY UNPINNED beyond hand-derived small graphs:
  *                         graph quality is checked, not an exact reference.
+ *   oracle_hnsw_build_p   the same construction under any L_bp, 0 < bp <= 2
+ *                         (the fixed-p HNSW of Section 4.3, one graph per p)
  *   oracle_hnsw_search    KnnSearch(q, t) on a CSR graph (Section 2.2 and
  *                         Section 3.1 "Candidate generation"; HNSW
- *                         Algorithms 2 and 5)
+ *                         Algorithms 2 and 5); oracle_hnsw_search_p under
+ *                         any L_bp
  *   oracle_verify_exact   top-K by L_p over the whole candidate set C, with
  *                         or without abandoning a candidate whose partial
  *                         sum exceeds the running K-th best sum
@@ -32,14 +35,17 @@
  *                         p in {1, 2} (Section 3 introduction); with graphs
  *                         under L0.5 and L1 and cutoff 0.6 it is U-HNSW-E
  *                         (Section 4.6), whose direct K-NN is for p in
- *                         {0.5, 1}
+ *                         {0.5, 1}; oracle_uhnsw_query_p takes the two
+ *                         graphs' p instead of metric codes
  *
  * Order used everywhere: lexicographic (distance, id), ids ascending on ties.
  * Base metrics (metric codes): 1 = L1, sum |d_j|; 2 = the squared L2 sum
  * d_j^2, which orders points exactly like L2; 3 = L0.5 without its root,
  * sum |d_j|^(1/2), which orders points exactly like L0.5; 4 = L1.5 without
  * its root, sum |d_j|^(3/2) (the fixed-p HNSW graph of Section 4.3 at
- * p = 1.5, where the paper finds plain HNSW faster).
+ * p = 1.5, where the paper finds plain HNSW faster).  The _p entry points
+ * take the base p itself: a graph built under L_bp is built and searched
+ * with S_bp = sum |d_j|^bp, which orders points exactly like L_bp.
  */
 #include <math.h>
 #include <stdint.h>
@@ -64,25 +70,40 @@ double oracle_lp_sum(const float* x, const float* q, int32_t d, double p) {
   return s;
 }
 
-/* Base metric: metric 1 -> L1 sum |d_j|; metric 2 -> squared L2 sum d_j^2;
- * metric 3 -> L0.5 sum |d_j|^(1/2); metric 4 -> L1.5 sum |d_j|^(3/2). */
-double oracle_base_dist(const float* x, const float* q, int32_t d, int32_t metric) {
+/* The base metric of a graph built under L_bp: S_bp = sum_j |d_j|^bp, with
+ * the closed forms of p = 1, 2, 0.5 and 1.5 written out and pow() for any
+ * other bp.  Every graph is built and searched with the S of its own bp. */
+static double base_dist_p(const float* x, const float* q, int32_t d, double bp) {
   double s = 0.0;
   for (int32_t j = 0; j < d; ++j) {
     double diff = (double)x[j] - (double)q[j];
-    if (metric == 1) s += fabs(diff);
-    else if (metric == 3) s += sqrt(fabs(diff));
-    else if (metric == 4) s += fabs(diff) * sqrt(fabs(diff));
-    else s += diff * diff;
+    double a = fabs(diff);
+    if (bp == 1.0) s += a;
+    else if (bp == 2.0) s += diff * diff;
+    else if (bp == 0.5) s += sqrt(a);
+    else if (bp == 1.5) s += a * sqrt(a);
+    else s += pow(a, bp);
   }
   return s;
 }
 
-/* The p of a base metric, and whether the code is one. */
+/* The p of a base metric code, and whether the code is one. */
 static double metric_p(int32_t metric) {
   return metric == 1 ? 1.0 : metric == 2 ? 2.0 : metric == 3 ? 0.5 : 1.5;
 }
 static int valid_metric(int32_t metric) { return metric >= 1 && metric <= 4; }
+static int valid_bp(double bp) { return bp > 0.0 && bp <= 2.0; }
+
+/* Base metric by code: metric 1 -> L1 sum |d_j|; metric 2 -> squared L2 sum
+ * d_j^2; metric 3 -> L0.5 sum |d_j|^(1/2); metric 4 -> L1.5 sum |d_j|^(3/2). */
+double oracle_base_dist(const float* x, const float* q, int32_t d, int32_t metric) {
+  return base_dist_p(x, q, d, metric_p(metric));
+}
+
+/* S^(1/bp): the distance a direct query on a graph built under L_bp returns */
+static double base_root(double s, double bp) {
+  return bp == 1.0 ? s : bp == 2.0 ? sqrt(s) : bp == 0.5 ? s * s : pow(s, 1.0 / bp);
+}
 
 /* (da, ia) precedes (db, ib) in the (distance, id) order */
 static int pair_less(double da, int64_t ia, double db, int64_t ib) {
@@ -246,7 +267,7 @@ static void visited_next(visited_t* v) {
  * evaluations.  q is either a query vector or, during construction, the
  * inserted row.
  */
-static int search_layer(const gview_t* g, const float* base, int32_t d, int32_t metric,
+static int search_layer(const gview_t* g, const float* base, int32_t d, double bp,
                         const float* q, const int64_t* ep, const double* ep_d, int32_t n_ep,
                         int32_t ef, int32_t lc, visited_t* vis, pset_t* W, int64_t* n_dist) {
   pset_t C = {0};
@@ -279,7 +300,7 @@ static int search_layer(const gview_t* g, const float* base, int32_t d, int32_t 
       if (e < 0) continue;
       if (vis->mark[e] == vis->gen) continue;
       vis->mark[e] = vis->gen;
-      double de = oracle_base_dist(base + e * (int64_t)d, q, d, metric);
+      double de = base_dist_p(base + e * (int64_t)d, q, d, bp);
       if (n_dist) (*n_dist)++;
       if (W->cnt < ef || pair_less(de, e, W->d[W->cnt - 1], W->id[W->cnt - 1])) {
         if (!pset_grow(&C, C.cnt + 1)) return 0;
@@ -302,14 +323,14 @@ static int search_layer(const gview_t* g, const float* base, int32_t d, int32_t 
 
 /* cand (cand_d = distance to the base point b) sorted ascending; keep e only
  * if e is strictly nearer to b than to every element already kept. */
-static int32_t select_heuristic(const float* base, int32_t d, int32_t metric, const int64_t* cand,
+static int32_t select_heuristic(const float* base, int32_t d, double bp, const int64_t* cand,
                                 const double* cand_d, int32_t nc, int32_t m, int32_t* out) {
   int32_t r = 0;
   for (int32_t i = 0; i < nc && r < m; ++i) {
     int64_t e = cand[i];
     int keep = 1;
     for (int32_t j = 0; j < r; ++j) {
-      double der = oracle_base_dist(base + e * (int64_t)d, base + (int64_t)out[j] * d, d, metric);
+      double der = base_dist_p(base + e * (int64_t)d, base + (int64_t)out[j] * d, d, bp);
       if (!(cand_d[i] < der)) { keep = 0; break; }
     }
     if (keep) out[r++] = (int32_t)e;
@@ -320,7 +341,7 @@ static int32_t select_heuristic(const float* base, int32_t d, int32_t metric, co
 /* exposed for the hand-derived tests of the heuristic */
 int32_t oracle_select_heuristic(const float* base, int32_t d, int32_t metric, const int64_t* cand,
                                 const double* cand_d, int32_t nc, int32_t m, int32_t* out) {
-  return select_heuristic(base, d, metric, cand, cand_d, nc, m, out);
+  return select_heuristic(base, d, metric_p(metric), cand, cand_d, nc, m, out);
 }
 
 /* ------------------------------------------------------------------ */
@@ -329,7 +350,8 @@ int32_t oracle_select_heuristic(const float* base, int32_t d, int32_t metric, co
 
 typedef struct {
   int64_t n;
-  int32_t d, metric, M, M0, efc;
+  int32_t d, M, M0, efc;
+  double bp;                       /* the graph's base metric is S_bp */
   int32_t entry, max_level;
   const float* base;
   int32_t* level;
@@ -370,13 +392,13 @@ void oracle_graph_free(oracle_graph* g) {
  *     ep <- W
  *   if l > L: entry point <- q
  */
-oracle_graph* oracle_hnsw_build(const float* base, int64_t n, int32_t d, int32_t metric, int32_t M,
-                                int32_t M0, int32_t efc, const int32_t* levels, int32_t* status) {
+oracle_graph* oracle_hnsw_build_p(const float* base, int64_t n, int32_t d, double bp, int32_t M,
+                                  int32_t M0, int32_t efc, const int32_t* levels, int32_t* status) {
   *status = OR_EINVAL;
-  if (n <= 0 || d <= 0 || !valid_metric(metric) || M < 2 || M0 < M || efc < 1) return NULL;
+  if (n <= 0 || d <= 0 || !valid_bp(bp) || M < 2 || M0 < M || efc < 1) return NULL;
   oracle_graph* g = (oracle_graph*)calloc(1, sizeof(oracle_graph));
   if (!g) { *status = OR_ENOMEM; return NULL; }
-  g->n = n; g->d = d; g->metric = metric; g->M = M; g->M0 = M0; g->efc = efc;
+  g->n = n; g->d = d; g->bp = bp; g->M = M; g->M0 = M0; g->efc = efc;
   g->base = base;
   g->level = (int32_t*)malloc(sizeof(int32_t) * n);
   g->links = (nlist_t**)calloc(n, sizeof(nlist_t*));
@@ -415,9 +437,9 @@ oracle_graph* oracle_hnsw_build(const float* base, int64_t n, int32_t d, int32_t
     int32_t L = g->max_level;
     int32_t n_ep = 1;
     ep[0] = g->entry;
-    epd[0] = oracle_base_dist(base + (int64_t)g->entry * d, x, d, metric);
+    epd[0] = base_dist_p(base + (int64_t)g->entry * d, x, d, bp);
     for (int32_t lc = L; lc > l; --lc) {
-      if (!search_layer(&view, base, d, metric, x, ep, epd, n_ep, 1, lc, &vis, &W, NULL)) {
+      if (!search_layer(&view, base, d, bp, x, ep, epd, n_ep, 1, lc, &vis, &W, NULL)) {
         *status = OR_ENOMEM;
         goto fail;
       }
@@ -426,11 +448,11 @@ oracle_graph* oracle_hnsw_build(const float* base, int64_t n, int32_t d, int32_t
       n_ep = 1;
     }
     for (int32_t lc = (L < l ? L : l); lc >= 0; --lc) {
-      if (!search_layer(&view, base, d, metric, x, ep, epd, n_ep, efc, lc, &vis, &W, NULL)) {
+      if (!search_layer(&view, base, d, bp, x, ep, epd, n_ep, efc, lc, &vis, &W, NULL)) {
         *status = OR_ENOMEM;
         goto fail;
       }
-      int32_t r = select_heuristic(base, d, metric, W.id, W.d, W.cnt, M, sel);
+      int32_t r = select_heuristic(base, d, bp, W.id, W.d, W.cnt, M, sel);
       list_set(&g->links[q][lc], sel, r);
       int32_t mmax = (lc == 0) ? M0 : M;
       for (int32_t i = 0; i < r; ++i) {
@@ -442,7 +464,7 @@ oracle_graph* oracle_hnsw_build(const float* base, int64_t n, int32_t d, int32_t
           int32_t m = Le->cnt;
           for (int32_t a = 0; a < m; ++a) {
             int64_t id = Le->ids[a];
-            double dd = oracle_base_dist(base + id * (int64_t)d, xe, d, metric);
+            double dd = base_dist_p(base + id * (int64_t)d, xe, d, bp);
             int32_t pos = a;
             while (pos > 0 && pair_less(dd, id, cand_d[pos - 1], cand[pos - 1])) {
               cand_d[pos] = cand_d[pos - 1];
@@ -452,7 +474,7 @@ oracle_graph* oracle_hnsw_build(const float* base, int64_t n, int32_t d, int32_t
             cand_d[pos] = dd;
             cand[pos] = id;
           }
-          int32_t rr = select_heuristic(base, d, metric, cand, cand_d, m, mmax, sel2);
+          int32_t rr = select_heuristic(base, d, bp, cand, cand_d, m, mmax, sel2);
           list_set(Le, sel2, rr);
         }
       }
@@ -471,6 +493,12 @@ fail:
   free(vis.mark); free(W.d); free(W.id); free(ep); free(epd); free(cand); free(cand_d); free(sel); free(sel2);
   oracle_graph_free(g);
   return NULL;
+}
+
+oracle_graph* oracle_hnsw_build(const float* base, int64_t n, int32_t d, int32_t metric, int32_t M,
+                                int32_t M0, int32_t efc, const int32_t* levels, int32_t* status) {
+  if (!valid_metric(metric)) { *status = OR_EINVAL; return NULL; }
+  return oracle_hnsw_build_p(base, n, d, metric_p(metric), M, M0, efc, levels, status);
 }
 
 /* CSR export: number of levels, entry point, and per-level sizes / arrays. */
@@ -510,26 +538,26 @@ void oracle_graph_level_copy(const oracle_graph* g, int32_t l, int32_t* nodes, i
  * ep <- nearest of W; W <- SEARCH-LAYER(q, ep, ef, 0); return the t nearest
  * of W ascending by (base distance, id).  Rows of out_ids beyond |W| are -1.
  */
-int oracle_hnsw_search(const oracle_csr* g, const float* base, int32_t d, int32_t metric,
-                       const float* q, int32_t ef, int32_t t, int64_t* out_ids, double* out_d,
-                       int64_t* n_dist) {
-  if (ef < 1 || t < 1 || !valid_metric(metric)) return OR_EINVAL;
+int oracle_hnsw_search_p(const oracle_csr* g, const float* base, int32_t d, double bp,
+                         const float* q, int32_t ef, int32_t t, int64_t* out_ids, double* out_d,
+                         int64_t* n_dist) {
+  if (ef < 1 || t < 1 || !valid_bp(bp)) return OR_EINVAL;
   gview_t view = {NULL, NULL, g};
   visited_t vis = {(uint32_t*)calloc(g->n, sizeof(uint32_t)), 0, g->n};
   pset_t W = {0};
   if (!vis.mark) return OR_ENOMEM;
   int64_t ep = g->entry_point;
-  double epd = oracle_base_dist(base + ep * (int64_t)d, q, d, metric);
+  double epd = base_dist_p(base + ep * (int64_t)d, q, d, bp);
   if (n_dist) (*n_dist)++;
   for (int32_t lc = g->num_levels - 1; lc >= 1; --lc) {
-    if (!search_layer(&view, base, d, metric, q, &ep, &epd, 1, 1, lc, &vis, &W, n_dist)) {
+    if (!search_layer(&view, base, d, bp, q, &ep, &epd, 1, 1, lc, &vis, &W, n_dist)) {
       free(vis.mark);
       return OR_ENOMEM;
     }
     ep = W.id[0];
     epd = W.d[0];
   }
-  if (!search_layer(&view, base, d, metric, q, &ep, &epd, 1, ef, 0, &vis, &W, n_dist)) {
+  if (!search_layer(&view, base, d, bp, q, &ep, &epd, 1, ef, 0, &vis, &W, n_dist)) {
     free(vis.mark);
     return OR_ENOMEM;
   }
@@ -541,6 +569,13 @@ int oracle_hnsw_search(const oracle_csr* g, const float* base, int32_t d, int32_
   free(W.d);
   free(W.id);
   return OR_OK;
+}
+
+int oracle_hnsw_search(const oracle_csr* g, const float* base, int32_t d, int32_t metric,
+                       const float* q, int32_t ef, int32_t t, int64_t* out_ids, double* out_d,
+                       int64_t* n_dist) {
+  if (!valid_metric(metric)) return OR_EINVAL;
+  return oracle_hnsw_search_p(g, base, d, metric_p(metric), q, ef, t, out_ids, out_d, n_dist);
 }
 
 /* ------------------------------------------------------------------ */
@@ -649,24 +684,24 @@ int oracle_verify_paper(const float* base, int32_t d, const float* q, double p, 
  * ma and mb (U-HNSW: L1 and L2; U-HNSW-E: L0.5 and L1): when p equals a
  * graph's base p exactly (in FP32), direct K-NN on that graph with
  * ef' = max(ef, k), and the returned distance is the base distance's root
- * S^(1/p_base).  Otherwise ga if p <= cutoff (FP32 compare), else gb;
+ * S^(1/bp).  Otherwise ga if p <= cutoff (FP32 compare), else gb;
  * C <- KnnSearch(q, t) with t' = max(t or ef, k) and ef' = max(ef, t'); then
  * verify C (mode 0: exact with abandon; mode 1: Algorithm 1's batches).  The
  * returned distance is S^(1/p).  Counters: stats[0] = base-distance
  * evaluations (N_b), stats[1] = L_p candidates computed (N_p), stats[2] = L_p
  * terms.
  */
-int oracle_uhnsw_query(const oracle_csr* ga, const oracle_csr* gb, int32_t ma, int32_t mb,
-                       const float* base, int32_t d, const float* q, float p, int32_t k,
-                       int32_t ef, int32_t t, float tau, int32_t kappa, float cutoff,
-                       int32_t mode, int64_t* out_ids, double* out_dist, int64_t* stats) {
+int oracle_uhnsw_query_p(const oracle_csr* ga, const oracle_csr* gb, double bpa, double bpb,
+                         const float* base, int32_t d, const float* q, float p, int32_t k,
+                         int32_t ef, int32_t t, float tau, int32_t kappa, float cutoff,
+                         int32_t mode, int64_t* out_ids, double* out_dist, int64_t* stats) {
   if (k < 1 || ef < 1 || !(p > 0.0f) || !(p <= 2.0f)) return OR_EINVAL;
-  if (!valid_metric(ma) || !valid_metric(mb)) return OR_EINVAL;
+  if (!valid_bp(bpa) || !valid_bp(bpb)) return OR_EINVAL;
   int64_t nb = 0, np = 0, nterm = 0;
-  const float pa = (float)metric_p(ma), pb = (float)metric_p(mb);
+  const float pa = (float)bpa, pb = (float)bpb;
   int use_a = (p == pa) ? 1 : (p == pb) ? 0 : (p <= cutoff);
-  int32_t metric = use_a ? ma : mb;
-  int direct = p == (float)metric_p(metric);
+  double bp = use_a ? bpa : bpb;
+  int direct = p == (float)bp;
   const oracle_csr* g = use_a ? ga : gb;
   int32_t tt = direct ? k : (t > 0 ? t : ef);
   if (tt < k) tt = k;
@@ -676,16 +711,12 @@ int oracle_uhnsw_query(const oracle_csr* ga, const oracle_csr* gb, int32_t ma, i
   int32_t* C32 = (int32_t*)malloc(sizeof(int32_t) * tt);
   double* S = (double*)malloc(sizeof(double) * k);
   if (!C || !Cd || !C32 || !S) { free(C); free(Cd); free(C32); free(S); return OR_ENOMEM; }
-  int rc = oracle_hnsw_search(g, base, d, metric, q, efp, tt, C, Cd, &nb);
+  int rc = oracle_hnsw_search_p(g, base, d, bp, q, efp, tt, C, Cd, &nb);
   if (rc != OR_OK) { free(C); free(Cd); free(C32); free(S); return rc; }
   if (direct) {
     for (int32_t j = 0; j < k; ++j) {
       out_ids[j] = C[j];
-      out_dist[j] = C[j] < 0 ? INFINITY
-                    : metric == 1 ? Cd[j]
-                    : metric == 2 ? sqrt(Cd[j])
-                    : metric == 3 ? Cd[j] * Cd[j]
-                                  : pow(Cd[j], 1.0 / 1.5);
+      out_dist[j] = C[j] < 0 ? INFINITY : base_root(Cd[j], bp);
     }
   } else {
     for (int32_t j = 0; j < tt; ++j) C32[j] = (int32_t)C[j];
@@ -703,4 +734,13 @@ int oracle_uhnsw_query(const oracle_csr* ga, const oracle_csr* gb, int32_t ma, i
   if (stats) { stats[0] = nb; stats[1] = np; stats[2] = nterm; }
   free(C); free(Cd); free(C32); free(S);
   return OR_OK;
+}
+
+int oracle_uhnsw_query(const oracle_csr* ga, const oracle_csr* gb, int32_t ma, int32_t mb,
+                       const float* base, int32_t d, const float* q, float p, int32_t k,
+                       int32_t ef, int32_t t, float tau, int32_t kappa, float cutoff,
+                       int32_t mode, int64_t* out_ids, double* out_dist, int64_t* stats) {
+  if (!valid_metric(ma) || !valid_metric(mb)) return OR_EINVAL;
+  return oracle_uhnsw_query_p(ga, gb, metric_p(ma), metric_p(mb), base, d, q, p, k, ef, t, tau,
+                              kappa, cutoff, mode, out_ids, out_dist, stats);
 }

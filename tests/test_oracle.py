@@ -475,3 +475,72 @@ def test_l15_graph_direct_queries_are_exact_at_full_beam():
         np.testing.assert_array_equal(ids[i], order)
         np.testing.assert_allclose(dist[i], D[i, order], rtol=1e-12)
     assert (st[:, 1] == 0).all()
+
+
+# ----------------------------------------------------------------- fixed-p HNSW at any p (Section 4.3)
+def _np_lp(Q, X, p):
+    """S_p = sum_j |x_j - q_j|^p in float64, written out with numpy."""
+    return (np.abs(Q.astype(np.float64)[:, None, :] - X.astype(np.float64)[None, :, :]) ** p).sum(-1)
+
+
+def test_lp_graph_heuristic_depends_on_p_by_hand():
+    """Three points inserted in order r=(0.9,-1.1), e=(2,0), q=(0,0).  From q,
+    e - q = (2, 0) is sparse and e - r = (1.1, 1.1) is spread, so e is nearer
+    q than r exactly when 2^p < 2 * 1.1^p, i.e. p < ln 2 / ln(2 / 1.1) ~ 1.159.
+    Under L0.8 e is q's nearest and r survives the heuristic (S(r,q) = 1.998 <
+    S(r,e) = 2.158), so q links to both; under L1.5 r is nearest and e is
+    dropped (S(e,q) = 2.828 > S(e,r) = 2.307).  A wrong exponent (1/p, or the
+    root taken inside the sum) lands on the other side of 1.159 for one of
+    the two."""
+    base = np.array([[0.9, -1.1], [2.0, 0.0], [0.0, 0.0]], np.float32)
+    lv = np.zeros(3, np.int32)
+    g = oracle.hnsw_build(base, None, M=2, ef_construction=10, levels=lv, M0=4, base_p=0.8)
+    assert _lists(g, 0) == {0: [1, 2], 1: [0, 2], 2: [1, 0]}
+    g = oracle.hnsw_build(base, None, M=2, ef_construction=10, levels=lv, M0=4, base_p=1.5)
+    assert _lists(g, 0) == {0: [1, 2], 1: [0], 2: [0]}
+
+
+def test_lp_graph_codes_are_special_cases():
+    """Building under base_p 1, 2, 0.5 and 1.5 gives the same graph as the
+    metric codes 1, 2, 3 and 4."""
+    w = I.WORKLOADS["mixture10k"].scaled(n=600, nq=2)
+    base = I.base_vectors(w)
+    lv = I.graph_levels(w, 2)
+    for code, bp in ((1, 1.0), (2, 2.0), (3, 0.5), (4, 1.5)):
+        a = oracle.hnsw_build(base, code, w.M, w.ef_construction, lv)
+        b = oracle.hnsw_build(base, None, w.M, w.ef_construction, lv, base_p=bp)
+        assert a["entry_point"] == b["entry_point"]
+        for la, lb in zip(a["levels"], b["levels"]):
+            for key in ("nodes", "offsets", "nbrs"):
+                np.testing.assert_array_equal(la[key], lb[key])
+
+
+@pytest.mark.parametrize("bp", [0.8, 1.2])
+def test_lp_graph_direct_and_verified_queries_at_full_beam(bp):
+    """A fixed HNSW under L_bp (the same graph in both slots) answers p = bp
+    directly, with distances S^(1/bp) and no L_p verification; any other p
+    goes through verification of the whole candidate set.  With ef = t = N
+    both are the exact top-K, against numpy brute force."""
+    w = I.WORKLOADS["mixture10k"].scaled(n=1200, nq=4)
+    base = I.base_vectors(w)
+    qs = I.query_vectors(w)
+    bp32 = float(np.float32(bp))
+    g = oracle.hnsw_build(base, None, w.M, w.ef_construction, I.graph_levels(w, 2), base_p=bp)
+    n = len(base)
+    assert _bfs_reach(g, g["entry_point"]).all()
+    for p, direct in ((bp32, True), (float(np.float32(1.37)), False)):
+        S = _np_lp(qs, base, p)
+        ids, dist, st = oracle.uhnsw_batch(g, g, base, qs, p, 10, n, t=n, tau=1.5,
+                                           base_p=(bp, bp))
+        for i in range(len(qs)):
+            order = np.lexsort((np.arange(n), S[i]))[:10]
+            np.testing.assert_array_equal(ids[i], order)
+            np.testing.assert_allclose(dist[i], S[i, order] ** (1.0 / p), rtol=1e-12)
+        assert ((st[:, 1] == 0) if direct else (st[:, 1] == n)).all()
+
+
+def test_lp_graph_rejects_bad_p():
+    base = np.zeros((4, 2), np.float32)
+    for bp in (0.0, -1.0, 2.5):
+        with pytest.raises(ValueError):
+            oracle.hnsw_build(base, None, 2, 10, np.zeros(4, np.int32), base_p=bp)
