@@ -85,12 +85,15 @@ typedef struct {
 
 /* Base metric of a graph (the metric it was built under and is searched
  * with).  UHNSW_BASE_L2 is the squared L2 sum and UHNSW_BASE_L05 the L0.5 sum
- * without its root; each orders points exactly like its L_p metric. */
+ * without its root; each orders points exactly like its L_p metric.
+ * UHNSW_BASE_LP is the sum for any other p in (0, 2] (the fixed-p HNSW of
+ * Section 4.3, one graph per p), evaluated as 2^(p log2 |d_j|). */
 typedef enum {
   UHNSW_BASE_L1 = 1,   /* sum |d_j|,       p = 1   */
   UHNSW_BASE_L2 = 2,   /* sum d_j^2,       p = 2   */
   UHNSW_BASE_L05 = 3,  /* sum |d_j|^(1/2), p = 0.5 */
-  UHNSW_BASE_L15 = 4   /* sum |d_j|^(3/2), p = 1.5 (a fixed-p HNSW graph, Section 4.3) */
+  UHNSW_BASE_L15 = 4,  /* sum |d_j|^(3/2), p = 1.5 (a fixed-p HNSW graph, Section 4.3) */
+  UHNSW_BASE_LP = 5    /* sum |d_j|^p,     p = uhnsw_load_opts.base_p of the slot */
 } uhnsw_base_metric;
 
 typedef struct {
@@ -103,7 +106,10 @@ typedef struct {
    * L1 as g2 ({UHNSW_BASE_L05, UHNSW_BASE_L1}) and searches with cutoff 0.6.
    * The first slot's base p must be below the second's. */
   int32_t base_metric[2];
-  int32_t reserved[5];
+  /* the p of a slot whose base_metric is UHNSW_BASE_LP, 0 < p <= 2 (read for
+   * that slot only; p = 1, 2, 0.5 or 1.5 act as their own codes) */
+  float base_p[2];
+  int32_t reserved[3];
 } uhnsw_load_opts;
 
 /* per-query counters written when uhnsw_search_opts.stats is set */
@@ -456,6 +462,22 @@ int uhnsw_build_graph(const float* base, int64_t n, int32_t d, int32_t metric, i
  */
 int uhnsw_build_graph_gpu(const float* base, int64_t n, int32_t d, int32_t metric, int32_t M,
                           int32_t ef_construction, const int32_t* levels, uhnsw_built** out);
+
+/*
+ * Build one HNSW graph under L_p for any 0 < p <= 2 (the fixed-p HNSW of
+ * Section 4.3: a graph per p, searched directly at that p).  The graph is
+ * built with S_p = sum_j |d_j|^p, which orders points exactly like L_p; p =
+ * 1, 2, 0.5 and 1.5 use their own closed forms (metric codes 1-4), any other
+ * p a power (std::pow on the host, the fast power intrinsic on the device).
+ * Load it with base_metric UHNSW_BASE_LP and base_p = p in its slot.
+ *   on_device  0: uhnsw_build_graph on the host with `threads` workers;
+ *              1: uhnsw_build_graph_gpu on the current CUDA device
+ * Other arguments as uhnsw_build_graph.  Errors: EINVAL (p outside (0, 2],
+ * or as the builder chosen), EOOM, ECUDA, ECAPACITY.
+ */
+int uhnsw_build_graph_lp(const float* base, int64_t n, int32_t d, float p, int32_t M,
+                         int32_t ef_construction, const int32_t* levels, int32_t threads,
+                         int32_t on_device, uhnsw_built** out);
 
 /* Fills `view` with host pointers into the built graph (valid until
  * uhnsw_built_free); level 0 lists every node, so level_nodes[0] is NULL. */

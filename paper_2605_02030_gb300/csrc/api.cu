@@ -84,6 +84,7 @@ struct uhnsw_index {
   uhnsw_dtype tdtype = UHNSW_F32;
   bool trav_exact = true;  // the traversal copy reproduces every FP32 value
   int32_t gmetric[2] = {UHNSW_BASE_L1, UHNSW_BASE_L2};  // base metric of each graph slot
+  float gp[2] = {1.f, 2.f};       // the p of each slot's base metric
   float* base32 = nullptr;
   void* trav = nullptr;
   DevGraph g[2];
@@ -230,9 +231,9 @@ GraphDev to_dev(const DevGraph& g) {
 
 constexpr int kBlock = 128;
 
-// The p of a base metric (uhnsw_base_metric).
-double base_metric_p(int32_t m) {
-  return m == UHNSW_BASE_L1 ? 1.0 : m == UHNSW_BASE_L2 ? 2.0 : m == UHNSW_BASE_L05 ? 0.5 : 1.5;
+// The p of a base metric code 1-4 (uhnsw_base_metric).
+float base_metric_p(int32_t m) {
+  return m == UHNSW_BASE_L1 ? 1.f : m == UHNSW_BASE_L2 ? 2.f : m == UHNSW_BASE_L05 ? 0.5f : 1.5f;
 }
 
 }  // namespace
@@ -252,14 +253,24 @@ extern "C" int uhnsw_load(const float* base, int64_t n, int32_t d, const uhnsw_g
   if (dt != UHNSW_F32 && dt != UHNSW_F16 && dt != UHNSW_BF16)
     return fail(UHNSW_EINVAL, "uhnsw_load: unknown traverse dtype %d", (int)dt);
   int32_t gm[2] = {UHNSW_BASE_L1, UHNSW_BASE_L2};
+  float gp[2] = {1.f, 2.f};
   for (int i = 0; i < 2; ++i) {
     const int32_t m = opts ? opts->base_metric[i] : 0;
     if (m == 0) continue;
-    if (m < UHNSW_BASE_L1 || m > UHNSW_BASE_L15)
+    if (m < UHNSW_BASE_L1 || m > UHNSW_BASE_LP)
       return fail(UHNSW_EINVAL, "uhnsw_load: base_metric[%d]=%d is not a uhnsw_base_metric", i, m);
-    gm[i] = m;
+    if (m == UHNSW_BASE_LP) {
+      const float bp = opts->base_p[i];
+      if (!(bp > 0.f && bp <= 2.f))
+        return fail(UHNSW_EINVAL, "uhnsw_load: base_p[%d]=%g outside (0, 2]", i, (double)bp);
+      gm[i] = uhnsw_internal::base_metric_of_p(bp);
+      gp[i] = bp;
+    } else {
+      gm[i] = m;
+      gp[i] = base_metric_p(m);
+    }
   }
-  if (!(base_metric_p(gm[0]) < base_metric_p(gm[1])))
+  if (!(gp[0] < gp[1]))
     return fail(UHNSW_EINVAL, "uhnsw_load: the first graph's base p must be below the second's");
 
   std::vector<int32_t> ell[2], upr[2], upa[2];
@@ -290,8 +301,10 @@ extern "C" int uhnsw_load(const float* base, int64_t n, int32_t d, const uhnsw_g
   idx->d = d;
   idx->d_pad = (d + 7) / 8 * 8;
   idx->tdtype = dt;
-  idx->gmetric[0] = gm[0];
-  idx->gmetric[1] = gm[1];
+  for (int i = 0; i < 2; ++i) {
+    idx->gmetric[i] = gm[i];
+    idx->gp[i] = gp[i];
+  }
   int rc = UHNSW_OK;
   const size_t row32 = (size_t)idx->d_pad * 4;
   do {
@@ -463,7 +476,7 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   a.g[1] = to_dev(idx->g[1]);
   for (int i = 0; i < 2; ++i) {
     a.gmetric[i] = idx->gmetric[i];
-    a.gp[i] = (float)base_metric_p(idx->gmetric[i]);
+    a.gp[i] = idx->gp[i];
   }
   a.q = q;
   a.p = p;
@@ -825,7 +838,7 @@ extern "C" int uhnsw_idealized_recall(uhnsw_index* idx, const float* q, const fl
   float* pb = (float*)s; s += al(b_pb);
   float* pd = (float*)s;
   cudaStream_t st = (cudaStream_t)stream;
-  const float gp0 = (float)base_metric_p(idx->gmetric[0]), gp1 = (float)base_metric_p(idx->gmetric[1]);
+  const float gp0 = idx->gp[0], gp1 = idx->gp[1];
   // exact L_p top-K, exact base-metric top-t_max, then the curves
   e = launch_exact(idx->base32, idx->n, idx->d, idx->d_pad, q, p, nq, K, ns, pd,
                    (int32_t*)((char*)pd + (size_t)ns * nq * K * 4), ik, dk, st);

@@ -59,13 +59,15 @@ struct BuildArgs {
   int32_t* err;            // [0] error code, [1] dropped incoming links
   int64_t n, rows;
   int32_t d_pad, metric, M, M0, efc, hb;
+  float bp;                // the p of metric 5
 };
 
 // Sum of the base-metric terms of two rows by a team of 8 lanes (each lane
 // 4 elements per 32), combined over the team by a butterfly: every lane of
-// the team ends with the sum.  b may point to shared memory.
+// the team ends with the sum.  b may point to shared memory.  Metric 5 takes
+// |d_j|^bp through the fast power intrinsic.
 __device__ __forceinline__ float team_dist(const float* __restrict__ a, const float* b, int d_pad,
-                                           int lt, int metric) {
+                                           int lt, int metric, float bp) {
   float acc = 0.f;
   for (int j = lt * 4; j < d_pad; j += 32) {
     const float4 x = *reinterpret_cast<const float4*>(a + j);
@@ -77,6 +79,7 @@ __device__ __forceinline__ float team_dist(const float* __restrict__ a, const fl
       acc += metric == UHNSW_BASE_L1    ? v
              : metric == UHNSW_BASE_L05 ? sqrtf(v)
              : metric == UHNSW_BASE_L15 ? v * sqrtf(v)
+             : metric == UHNSW_BASE_LP  ? __powf(v, bp)
                                         : v * v;
     }
   }
@@ -93,7 +96,7 @@ __device__ __forceinline__ void warp_dists(const BuildArgs& a, const float* x, c
   for (int i0 = 0; i0 < m; i0 += 4) {
     const int i = min(i0 + team, m - 1);
     const int64_t v = chk_idx((int64_t)(ids[i] & kIdMask), a.n, 20, a.err);
-    const float s = team_dist(a.X + v * a.d_pad, x, a.d_pad, lt, a.metric);
+    const float s = team_dist(a.X + v * a.d_pad, x, a.d_pad, lt, a.metric, a.bp);
     if (lt == 0 && i0 + team < m) out[i0 + team] = s;
   }
   __syncwarp();
@@ -114,7 +117,7 @@ __device__ int warp_select(const BuildArgs& a, const float* cd, const uint32_t* 
     for (int j0 = 0; j0 < r && keep; j0 += 4) {
       const int j = min(j0 + team, r - 1);
       const int64_t s = chk_idx((int64_t)sel[j], a.n, 22, a.err);
-      const float ds = team_dist(xc, a.X + s * a.d_pad, a.d_pad, lt, a.metric);
+      const float ds = team_dist(xc, a.X + s * a.d_pad, a.d_pad, lt, a.metric, a.bp);
       const bool bad = j0 + team < r && !(dc < ds);
       keep = !__any_sync(kFull, bad);
     }
@@ -386,15 +389,21 @@ int reverse_smem(int d_pad, int M0) {
 extern "C" int uhnsw_build_graph_gpu(const float* base, int64_t n, int32_t d, int32_t metric,
                                      int32_t M, int32_t ef_construction, const int32_t* levels,
                                      uhnsw_built** out) {
+  uhnsw_internal::clear_error();
+  if (!out) return uhnsw_internal::fail(UHNSW_EINVAL, "uhnsw_build_graph_gpu: out is NULL");
+  *out = nullptr;
+  if (metric < UHNSW_BASE_L1 || metric > UHNSW_BASE_L15)
+    return uhnsw_internal::fail(UHNSW_EINVAL, "uhnsw_build_graph_gpu: metric must be 1, 2, 3 or 4");
+  return uhnsw_internal::build_graph_gpu(base, n, d, metric, 0.f, M, ef_construction, levels, out);
+}
+
+int uhnsw_internal::build_graph_gpu(const float* base, int64_t n, int32_t d, int32_t metric,
+                                    float bp, int32_t M, int32_t ef_construction,
+                                    const int32_t* levels, uhnsw_built** out) {
   using namespace uhnsw_dev;
   using uhnsw_internal::fail;
-  uhnsw_internal::clear_error();
-  if (!out) return fail(UHNSW_EINVAL, "uhnsw_build_graph_gpu: out is NULL");
-  *out = nullptr;
   if (!base || !levels || n < 1 || n > INT32_MAX / 2 || d < 1 || d > UHNSW_MAX_DIM)
     return fail(UHNSW_EINVAL, "uhnsw_build_graph_gpu: bad base/levels/n/d");
-  if (metric < UHNSW_BASE_L1 || metric > UHNSW_BASE_L15)
-    return fail(UHNSW_EINVAL, "uhnsw_build_graph_gpu: metric must be 1, 2, 3 or 4");
   if (M < 2 || 2 * M > UHNSW_MAX_DEGREE || ef_construction < 1 || ef_construction > 512)
     return fail(UHNSW_EINVAL, "uhnsw_build_graph_gpu: need 2 <= M <= %d, 1 <= efc <= 512",
                 UHNSW_MAX_DEGREE / 2);
@@ -496,6 +505,7 @@ extern "C" int uhnsw_build_graph_gpu(const float* base, int64_t n, int32_t d, in
   a.rows = rows;
   a.d_pad = d_pad;
   a.metric = metric;
+  a.bp = bp;
   a.M = M;
   a.M0 = M0;
   a.efc = efc;

@@ -57,10 +57,11 @@ inline v4f load4(const float* p) {
 
 // Base metric in FP32: metric 1 -> sum |d_j|, metric 2 -> sum d_j^2,
 // metric 3 -> sum |d_j|^(1/2) (the L0.5 graph of U-HNSW-E, Section 4.6),
-// metric 4 -> sum |d_j|^(3/2) (an L1.5 graph, Section 4.3's fixed-p HNSW).
+// metric 4 -> sum |d_j|^(3/2) (an L1.5 graph, Section 4.3's fixed-p HNSW),
+// metric 5 -> sum |d_j|^bp (the fixed-p HNSW at any other p).
 // Four independent 4-wide partial sums, then a fixed combination order; the
 // same for every call, so the build is reproducible on one machine.
-float base_distance(const float* a, const float* b, int32_t d, int32_t metric) {
+float base_distance(const float* a, const float* b, int32_t d, int32_t metric, float bp) {
   v4f s0 = {0, 0, 0, 0}, s1 = s0, s2 = s0, s3 = s0;
   int32_t j = 0;
   if (metric == 1) {
@@ -87,6 +88,17 @@ float base_distance(const float* a, const float* b, int32_t d, int32_t metric) {
         s3[u] += metric == 3 ? std::sqrt(a3) : a3 * std::sqrt(a3);
       }
     }
+  } else if (metric == UHNSW_BASE_LP) {
+    for (; j + 16 <= d; j += 16) {
+      v4f x0 = load4(a + j) - load4(b + j), x1 = load4(a + j + 4) - load4(b + j + 4);
+      v4f x2 = load4(a + j + 8) - load4(b + j + 8), x3 = load4(a + j + 12) - load4(b + j + 12);
+      for (int u = 0; u < 4; ++u) {
+        s0[u] += std::pow(std::fabs(x0[u]), bp);
+        s1[u] += std::pow(std::fabs(x1[u]), bp);
+        s2[u] += std::pow(std::fabs(x2[u]), bp);
+        s3[u] += std::pow(std::fabs(x3[u]), bp);
+      }
+    }
   } else {
     for (; j + 16 <= d; j += 16) {
       v4f x0 = load4(a + j) - load4(b + j), x1 = load4(a + j + 4) - load4(b + j + 4);
@@ -102,7 +114,8 @@ float base_distance(const float* a, const float* b, int32_t d, int32_t metric) {
   for (; j < d; ++j) {
     float x = a[j] - b[j];
     const float a = std::fabs(x);
-    r += metric == 1 ? a : metric == 3 ? std::sqrt(a) : metric == 4 ? a * std::sqrt(a) : x * x;
+    r += metric == 1 ? a : metric == 3 ? std::sqrt(a) : metric == 4 ? a * std::sqrt(a)
+         : metric == UHNSW_BASE_LP ? std::pow(a, bp) : x * x;
   }
   return r;
 }
@@ -137,6 +150,7 @@ struct Visited {
 struct Builder {
   int64_t n;
   int32_t d, metric, M, M0, efc;
+  float bp = 0.f;                // the p of metric 5
   const float* base;
   std::vector<int32_t> level;
   std::vector<int32_t> links0;   // n x (M0 + 1): count, ids
@@ -152,7 +166,7 @@ struct Builder {
     return &links_up[(up_off[v] + l - 1) * (int64_t)(M + 1)];
   }
   const float* vec(int32_t v) const { return base + (int64_t)v * d; }
-  float dist(const float* x, int32_t v) const { return base_distance(x, vec(v), d, metric); }
+  float dist(const float* x, int32_t v) const { return base_distance(x, vec(v), d, metric, bp); }
 
   // SEARCH-LAYER from the entry set `ep` (distances known) with beam `ef` at
   // level lc; returns the result set ascending by (d, id).
@@ -208,7 +222,7 @@ struct Builder {
       const DI& e = cand[i];
       bool keep = true;
       for (int32_t j = 0; j < r; ++j) {
-        if (!(e.d < base_distance(vec(e.id), vec(out[j]), d, metric))) {
+        if (!(e.d < base_distance(vec(e.id), vec(out[j]), d, metric, bp))) {
           keep = false;
           break;
         }
@@ -285,16 +299,13 @@ struct uhnsw_built {
   std::vector<std::vector<int32_t>> nbrs;
 };
 
-extern "C" int uhnsw_build_graph(const float* base, int64_t n, int32_t d, int32_t metric,
-                                 int32_t M, int32_t ef_construction, const int32_t* levels,
-                                 int32_t threads, uhnsw_built** out) {
-  uhnsw_internal::clear_error();
-  if (!out) return uhnsw_internal::fail(UHNSW_EINVAL, "uhnsw_build_graph: out is NULL");
-  *out = nullptr;
+namespace {
+
+int build_host(const float* base, int64_t n, int32_t d, int32_t metric, float bp, int32_t M,
+               int32_t ef_construction, const int32_t* levels, int32_t threads,
+               uhnsw_built** out) {
   if (!base || !levels || n < 1 || n > INT32_MAX || d < 1 || d > UHNSW_MAX_DIM)
     return uhnsw_internal::fail(UHNSW_EINVAL, "uhnsw_build_graph: bad base/levels/n/d");
-  if (metric < 1 || metric > 4)
-    return uhnsw_internal::fail(UHNSW_EINVAL, "uhnsw_build_graph: metric must be 1, 2, 3 or 4");
   if (M < 2 || 2 * M > UHNSW_MAX_DEGREE || ef_construction < 1)
     return uhnsw_internal::fail(UHNSW_EINVAL, "uhnsw_build_graph: need 2 <= M <= %d, efc >= 1",
                                 UHNSW_MAX_DEGREE / 2);
@@ -307,6 +318,7 @@ extern "C" int uhnsw_build_graph(const float* base, int64_t n, int32_t d, int32_
     B.n = n;
     B.d = d;
     B.metric = metric;
+    B.bp = bp;
     B.M = M;
     B.M0 = 2 * M;
     B.efc = ef_construction;
@@ -373,6 +385,34 @@ extern "C" int uhnsw_build_graph(const float* base, int64_t n, int32_t d, int32_
   } catch (const std::bad_alloc&) {
     return uhnsw_internal::fail(UHNSW_EOOM, "uhnsw_build_graph: out of host memory");
   }
+}
+
+}  // namespace
+
+extern "C" int uhnsw_build_graph(const float* base, int64_t n, int32_t d, int32_t metric,
+                                 int32_t M, int32_t ef_construction, const int32_t* levels,
+                                 int32_t threads, uhnsw_built** out) {
+  uhnsw_internal::clear_error();
+  if (!out) return uhnsw_internal::fail(UHNSW_EINVAL, "uhnsw_build_graph: out is NULL");
+  *out = nullptr;
+  if (metric < 1 || metric > 4)
+    return uhnsw_internal::fail(UHNSW_EINVAL, "uhnsw_build_graph: metric must be 1, 2, 3 or 4");
+  return build_host(base, n, d, metric, 0.f, M, ef_construction, levels, threads, out);
+}
+
+extern "C" int uhnsw_build_graph_lp(const float* base, int64_t n, int32_t d, float p, int32_t M,
+                                    int32_t ef_construction, const int32_t* levels,
+                                    int32_t threads, int32_t on_device, uhnsw_built** out) {
+  uhnsw_internal::clear_error();
+  if (!out) return uhnsw_internal::fail(UHNSW_EINVAL, "uhnsw_build_graph_lp: out is NULL");
+  *out = nullptr;
+  if (!(p > 0.f && p <= 2.f))
+    return uhnsw_internal::fail(UHNSW_EINVAL, "uhnsw_build_graph_lp: p=%g outside (0, 2]",
+                                (double)p);
+  const int32_t metric = uhnsw_internal::base_metric_of_p(p);
+  if (on_device)
+    return uhnsw_internal::build_graph_gpu(base, n, d, metric, p, M, ef_construction, levels, out);
+  return build_host(base, n, d, metric, p, M, ef_construction, levels, threads, out);
 }
 
 namespace uhnsw_internal {

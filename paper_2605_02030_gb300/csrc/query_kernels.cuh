@@ -92,16 +92,18 @@ struct QueryArgs {
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
 // Routing of a query (Algorithm 1, lines 1-5): the graph slot it searches,
-// whether it is answered directly (p is that graph's own base p), and the
-// slot's base metric.  p <= cutoff selects the first slot.
+// whether it is answered directly (p is that graph's own base p), the slot's
+// base metric and its p.  p <= cutoff selects the first slot.
 struct Route {
   int slot;
   bool direct;
   int metric;
+  float bp;
 };
 __device__ __forceinline__ Route route_query(const QueryArgs& a, float p) {
   const int slot = p == a.gp[0] ? 0 : p == a.gp[1] ? 1 : (p <= a.cutoff ? 0 : 1);
-  return Route{slot, p == a.gp[slot], a.gmetric[slot]};
+  const float bp = a.gp[slot];
+  return Route{slot, p == bp, a.gmetric[slot], bp};
 }
 
 // t and tau of query qi (per-query arrays when given).
@@ -114,12 +116,13 @@ __device__ __forceinline__ float query_tau(const QueryArgs& a, int64_t qi) {
   return v != 0.f ? v : 0.92f;
 }
 
-// The distance a direct query returns: the base sum's root S^(1/p_base).
-__device__ __forceinline__ float base_root(int metric, float s) {
+// The distance a direct query returns: the base sum's root S^(1/bp).
+__device__ __forceinline__ float base_root(int metric, float bp, float s) {
   return metric == UHNSW_BASE_L1    ? s
          : metric == UHNSW_BASE_L2  ? sqrtf(s)
          : metric == UHNSW_BASE_L05 ? (float)((double)s * (double)s)
-                                    : (float)pow((double)s, 1.0 / 1.5);
+         : metric == UHNSW_BASE_L15 ? (float)pow((double)s, 1.0 / 1.5)
+                                    : (float)pow((double)s, 1.0 / (double)bp);
 }
 
 // Dynamic shared-memory carve-up (byte offsets), identical on host and device.
@@ -221,7 +224,7 @@ template <typename T, int TEAM, int CPL, int BLOCK, int METRIC>
 __device__ __forceinline__ void dist_batch(const T* __restrict__ rows, int d_pad,
                                            const float (&qv)[CPL][Elems16<T>::n],
                                            const uint32_t* ids, float* out, int m, int64_t n,
-                                           int32_t* err) {
+                                           int32_t* err, float bp) {
   constexpr int VEC = Elems16<T>::n;
   constexpr int NT = BLOCK / TEAM;
   constexpr int U = 2;
@@ -255,6 +258,7 @@ __device__ __forceinline__ void dist_batch(const T* __restrict__ rows, int d_pad
           if (METRIC == UHNSW_BASE_L1) acc += fabsf(df);
           else if (METRIC == UHNSW_BASE_L05) acc += hw_sqrt(fabsf(df));
           else if (METRIC == UHNSW_BASE_L15) acc += fabsf(df) * hw_sqrt(fabsf(df));
+          else if (METRIC == UHNSW_BASE_LP) acc += hw_ex2(bp * hw_lg2(fabsf(df)));
           else acc = fmaf(df, df, acc);
         }
       }
@@ -267,14 +271,15 @@ __device__ __forceinline__ void dist_batch(const T* __restrict__ rows, int d_pad
 }
 
 template <typename T, int TEAM, int CPL, int BLOCK>
-__device__ __forceinline__ void dist_batch_metric(int metric, const T* rows, int d_pad,
+__device__ __forceinline__ void dist_batch_metric(int metric, float bp, const T* rows, int d_pad,
                                                   const float (&qv)[CPL][Elems16<T>::n],
                                                   const uint32_t* ids, float* out, int m,
                                                   int64_t n, int32_t* err) {
-  if (metric == UHNSW_BASE_L1) dist_batch<T, TEAM, CPL, BLOCK, 1>(rows, d_pad, qv, ids, out, m, n, err);
-  else if (metric == UHNSW_BASE_L2) dist_batch<T, TEAM, CPL, BLOCK, 2>(rows, d_pad, qv, ids, out, m, n, err);
-  else if (metric == UHNSW_BASE_L05) dist_batch<T, TEAM, CPL, BLOCK, 3>(rows, d_pad, qv, ids, out, m, n, err);
-  else dist_batch<T, TEAM, CPL, BLOCK, 4>(rows, d_pad, qv, ids, out, m, n, err);
+  if (metric == UHNSW_BASE_L1) dist_batch<T, TEAM, CPL, BLOCK, 1>(rows, d_pad, qv, ids, out, m, n, err, bp);
+  else if (metric == UHNSW_BASE_L2) dist_batch<T, TEAM, CPL, BLOCK, 2>(rows, d_pad, qv, ids, out, m, n, err, bp);
+  else if (metric == UHNSW_BASE_L05) dist_batch<T, TEAM, CPL, BLOCK, 3>(rows, d_pad, qv, ids, out, m, n, err, bp);
+  else if (metric == UHNSW_BASE_L15) dist_batch<T, TEAM, CPL, BLOCK, 4>(rows, d_pad, qv, ids, out, m, n, err, bp);
+  else dist_batch<T, TEAM, CPL, BLOCK, 5>(rows, d_pad, qv, ids, out, m, n, err, bp);
 }
 
 // ---------------------------------------------------------------- verification
@@ -552,7 +557,7 @@ __device__ void run_query(const QueryArgs& a, int64_t qi, unsigned char* smem, c
   // 2. greedy descent through the upper levels (HNSW search with beam 1)
   if (tid == 0) ci[0] = (uint32_t)g.entry;
   __syncthreads();
-  dist_batch_metric<T, TEAM, CPL, BLOCK>(metric, trav, a.d_pad, qv, ci, cd, 1, a.n, a.err);
+  dist_batch_metric<T, TEAM, CPL, BLOCK>(metric, rt.bp, trav, a.d_pad, qv, ci, cd, 1, a.n, a.err);
   __syncthreads();
   int cur = g.entry;
   float cur_d = cd[0];
@@ -577,7 +582,7 @@ __device__ void run_query(const QueryArgs& a, int64_t qi, unsigned char* smem, c
       const int m = s.m;
       nadj += 1;
       nb += m;
-      dist_batch_metric<T, TEAM, CPL, BLOCK>(metric, trav, a.d_pad, qv, ci, cd, m, a.n, a.err);
+      dist_batch_metric<T, TEAM, CPL, BLOCK>(metric, rt.bp, trav, a.d_pad, qv, ci, cd, m, a.n, a.err);
       __syncthreads();
       block_argmin<BLOCK>(cd, ci, m, s);
       if (m > 0 && pair_lt(s.bestd, s.besti, cur_d, cur)) {
@@ -651,7 +656,7 @@ __device__ void run_query(const QueryArgs& a, int64_t qi, unsigned char* smem, c
     nexp += npar;
     nadj += npar;
     nb += m;
-    dist_batch_metric<T, TEAM, CPL, BLOCK>(metric, trav, a.d_pad, qv, ci, cd, m, a.n, a.err);
+    dist_batch_metric<T, TEAM, CPL, BLOCK>(metric, rt.bp, trav, a.d_pad, qv, ci, cd, m, a.n, a.err);
     if (tid == 0) s.first = INT_MAX;
     __syncthreads();
     const int nbn = block_merge(bd[cb], bi[cb], bn, cd, ci, m, sd, si, bd[cb ^ 1], bi[cb ^ 1], efp,
@@ -686,7 +691,7 @@ __device__ void run_query(const QueryArgs& a, int64_t qi, unsigned char* smem, c
       if (j < k && j < bn) {
         oid[j] = (int64_t)(bi[cb][j] & kIdMask);
         const float dd = bd[cb][j];
-        odist[j] = base_root(metric, dd);
+        odist[j] = base_root(metric, rt.bp, dd);
       } else {
         oid[j] = -1;
         odist[j] = __int_as_float(0x7f800000);

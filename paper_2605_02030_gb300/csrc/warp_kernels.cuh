@@ -117,13 +117,13 @@ __device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
 }
 
 // Elementwise |x - q| (metric 1), (x - q)^2 (metric 2), |x - q|^(1/2)
-// (metric 3) or |x - q|^(3/2) (metric 4) summed over
+// (metric 3), |x - q|^(3/2) (metric 4) or |x - q|^bp (metric 5) summed over
 // one 16-byte chunk of a row, as even / odd element pairs accumulated into acc.
 // q holds the chunk's query values as FP32 pairs (little-endian: element 2e in
 // the low half).
 template <typename T, int METRIC>
 __device__ __forceinline__ void chunk_partial(const uint4& v, const uint64_t (&q)[Elems16<T>::n / 2],
-                                              uint64_t& acc) {
+                                              uint64_t& acc, float bp) {
   constexpr int VEC = Elems16<T>::n;
   float x[VEC];
   unpack16<T>(v, x);
@@ -142,6 +142,10 @@ __device__ __forceinline__ void chunk_partial(const uint4& v, const uint64_t (&q
       lo = fabsf(lo);
       hi = fabsf(hi);
       acc = f2_add(acc, f2_pack(lo * hw_sqrt(lo), hi * hw_sqrt(hi)));
+    } else if (METRIC == UHNSW_BASE_LP) {
+      float lo, hi;
+      asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(df));
+      acc = f2_add(acc, f2_pack(hw_ex2(bp * hw_lg2(fabsf(lo))), hw_ex2(bp * hw_lg2(fabsf(hi)))));
     } else {
       acc = f2_fma(df, df, acc);
     }
@@ -198,7 +202,7 @@ __device__ __forceinline__ void warp_stage_rows(const T* __restrict__ rows, int 
 template <typename T, int TEAM, int CPL, int U, int METRIC>
 __device__ __forceinline__ void warp_dist(const T* __restrict__ rows, int d_pad, const float* qs,
                                           const uint32_t* ids, float* out, int m, int64_t n,
-                                          int32_t* err) {
+                                          int32_t* err, float bp) {
   constexpr int VEC = Elems16<T>::n;
   constexpr int NT = 32 / TEAM;
   const int lane = threadIdx.x & 31;
@@ -243,7 +247,7 @@ __device__ __forceinline__ void warp_dist(const T* __restrict__ rows, int d_pad,
         for (int e = 0; e < VEC / 2; ++e) q[e] = 0ull;
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) chunk_partial<T, METRIC>(buf[u][c], q, acc[u]);
+      for (int u = 0; u < U; ++u) chunk_partial<T, METRIC>(buf[u][c], q, acc[u], bp);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -258,13 +262,14 @@ __device__ __forceinline__ void warp_dist(const T* __restrict__ rows, int d_pad,
 }
 
 template <typename T, int TEAM, int CPL, int U>
-__device__ __forceinline__ void warp_dist_metric(int metric, const T* rows, int d_pad,
+__device__ __forceinline__ void warp_dist_metric(int metric, float bp, const T* rows, int d_pad,
                                                  const float* qs, const uint32_t* ids, float* out,
                                                  int m, int64_t n, int32_t* err) {
-  if (metric == UHNSW_BASE_L1) warp_dist<T, TEAM, CPL, U, 1>(rows, d_pad, qs, ids, out, m, n, err);
-  else if (metric == UHNSW_BASE_L2) warp_dist<T, TEAM, CPL, U, 2>(rows, d_pad, qs, ids, out, m, n, err);
-  else if (metric == UHNSW_BASE_L05) warp_dist<T, TEAM, CPL, U, 3>(rows, d_pad, qs, ids, out, m, n, err);
-  else warp_dist<T, TEAM, CPL, U, 4>(rows, d_pad, qs, ids, out, m, n, err);
+  if (metric == UHNSW_BASE_L1) warp_dist<T, TEAM, CPL, U, 1>(rows, d_pad, qs, ids, out, m, n, err, bp);
+  else if (metric == UHNSW_BASE_L2) warp_dist<T, TEAM, CPL, U, 2>(rows, d_pad, qs, ids, out, m, n, err, bp);
+  else if (metric == UHNSW_BASE_L05) warp_dist<T, TEAM, CPL, U, 3>(rows, d_pad, qs, ids, out, m, n, err, bp);
+  else if (metric == UHNSW_BASE_L15) warp_dist<T, TEAM, CPL, U, 4>(rows, d_pad, qs, ids, out, m, n, err, bp);
+  else warp_dist<T, TEAM, CPL, U, 5>(rows, d_pad, qs, ids, out, m, n, err, bp);
 }
 
 // Drops the candidates that cannot enter a full W (those not before its last
@@ -522,7 +527,7 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
       if (lane == 0) set_error(a.err, UHNSW_ECAPACITY);
       break;
     }
-    warp_dist_metric<T, TEAM, CPL, U>(metric, trav, a.d_pad, qs, ci, cd, m, a.n, a.err);
+    warp_dist_metric<T, TEAM, CPL, U>(metric, rt.bp, trav, a.d_pad, qs, ci, cd, m, a.n, a.err);
     if (descending) {
       if (at_entry) {
         cur_d = cd[0];
@@ -658,7 +663,7 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
       if (j < k && j < bn) {
         oid[j] = (int64_t)(bic[j] & kIdMask);
         const float dd = bdc[j];
-        odist[j] = base_root(metric, dd);
+        odist[j] = base_root(metric, rt.bp, dd);
       } else {
         oid[j] = -1;
         odist[j] = kInf;

@@ -45,12 +45,12 @@ class _Graph(C.Structure):
 
 class _LoadOpts(C.Structure):
     _fields_ = [("traverse_dtype", C.c_int32), ("base_metric", C.c_int32 * 2),
-                ("reserved", C.c_int32 * 5)]
+                ("base_p", C.c_float * 2), ("reserved", C.c_int32 * 3)]
 
 
 # Base metrics (uhnsw_base_metric): 1 = L1, 2 = squared L2, 3 = L0.5 sum,
-# 4 = L1.5 sum.
-BASE_L1, BASE_L2, BASE_L05, BASE_L15 = 1, 2, 3, 4
+# 4 = L1.5 sum, 5 = the L_p sum of a slot's base_p (any 0 < p <= 2).
+BASE_L1, BASE_L2, BASE_L05, BASE_L15, BASE_LP = 1, 2, 3, 4, 5
 U_HNSW = (BASE_L1, BASE_L2)        # G1 and G2, cutoff 1.4
 U_HNSW_E = (BASE_L05, BASE_L1)     # G0.5 and G1, cutoff 0.6 (Section 4.6)
 
@@ -82,7 +82,8 @@ EXPORTS = ("uhnsw_load", "uhnsw_search", "uhnsw_search_host", "uhnsw_verify", "u
            "uhnsw_server_wait", "uhnsw_server_replay", "uhnsw_server_stats",
            "uhnsw_server_destroy", "uhnsw_autotune", "uhnsw_autotune_save", "uhnsw_autotune_load",
            "uhnsw_index_info", "uhnsw_device_status", "uhnsw_free", "uhnsw_last_error",
-           "uhnsw_build_graph", "uhnsw_build_graph_gpu", "uhnsw_built_graph", "uhnsw_built_free")
+           "uhnsw_build_graph", "uhnsw_build_graph_gpu", "uhnsw_build_graph_lp",
+           "uhnsw_built_graph", "uhnsw_built_free")
 
 
 def library_path() -> str:
@@ -147,6 +148,8 @@ def load_library():
     lib.uhnsw_build_graph.argtypes = [P, I64, I32, I32, I32, I32, P, I32, P]
     lib.uhnsw_build_graph_gpu.restype = C.c_int
     lib.uhnsw_build_graph_gpu.argtypes = [P, I64, I32, I32, I32, I32, P, P]
+    lib.uhnsw_build_graph_lp.restype = C.c_int
+    lib.uhnsw_build_graph_lp.argtypes = [P, I64, I32, C.c_float, I32, I32, P, I32, I32, P]
     lib.uhnsw_built_graph.restype = C.c_int
     lib.uhnsw_built_graph.argtypes = [P, P]
     lib.uhnsw_built_free.restype = None
@@ -176,26 +179,33 @@ def _stream_ptr(stream) -> C.c_void_p:
 
 # ----------------------------------------------------------------- graph building
 def build_graph(base: np.ndarray, metric: int, M: int, ef_construction: int, levels: np.ndarray,
-                threads: int = 0, device: str = "cpu") -> dict:
-    """HNSW graph under L1 (metric=1), squared L2 (metric=2) or the L0.5 sum
-    (metric=3, U-HNSW-E's G0.5), built on the host by the library's
-    multi-threaded insertion (device="cpu") or on the current CUDA device by
-    batched insertion (device="gpu"); returned as a CSR dict {num_levels,
-    entry_point, max_degree0, max_degree, n, levels: [{nodes, offsets,
-    nbrs}]} with level 0 listing every node."""
+                threads: int = 0, device: str = "cpu", p: float | None = None) -> dict:
+    """HNSW graph under L1 (metric=1), squared L2 (metric=2), the L0.5 sum
+    (metric=3, U-HNSW-E's G0.5), the L1.5 sum (metric=4) or, with
+    metric=BASE_LP and p given, the L_p sum for any 0 < p <= 2, built on the
+    host by the library's multi-threaded insertion (device="cpu") or on the
+    current CUDA device by batched insertion (device="gpu"); returned as a CSR
+    dict {num_levels, entry_point, max_degree0, max_degree, n, levels:
+    [{nodes, offsets, nbrs}]} with level 0 listing every node."""
     lib = load_library()
     base = np.ascontiguousarray(base, np.float32)
     levels = np.ascontiguousarray(levels, np.int32)
     n, d = base.shape
     h = C.c_void_p(0)
-    if device == "gpu":
+    if device not in ("cpu", "gpu"):
+        raise ValueError(f"device must be 'cpu' or 'gpu', not {device!r}")
+    if metric == BASE_LP:
+        if p is None:
+            raise ValueError("metric BASE_LP needs p")
+        _check(lib.uhnsw_build_graph_lp(_np_ptr(base), n, d, float(p), M, ef_construction,
+                                        _np_ptr(levels), threads, int(device == "gpu"),
+                                        C.byref(h)))
+    elif device == "gpu":
         _check(lib.uhnsw_build_graph_gpu(_np_ptr(base), n, d, metric, M, ef_construction,
                                          _np_ptr(levels), C.byref(h)))
-    elif device == "cpu":
+    else:
         _check(lib.uhnsw_build_graph(_np_ptr(base), n, d, metric, M, ef_construction,
                                      _np_ptr(levels), threads, C.byref(h)))
-    else:
-        raise ValueError(f"device must be 'cpu' or 'gpu', not {device!r}")
     try:
         g = _Graph()
         _check(lib.uhnsw_built_graph(h, C.byref(g)))
@@ -264,10 +274,12 @@ def plan_t(counts: np.ndarray, p: np.ndarray, K: int, target: float, p_lo: float
 class Index:
     """A loaded U-HNSW index (base vectors + two graphs) on the current CUDA
     device.  metrics: base metrics of g1 and g2, U_HNSW (G1, G2) by default or
-    U_HNSW_E (G0.5, G1; search with cutoff=0.6)."""
+    U_HNSW_E (G0.5, G1; search with cutoff=0.6).  A slot whose metric is
+    BASE_LP takes its p from base_p (e.g. metrics=(BASE_LP, BASE_L2),
+    base_p=(0.8, 0) for a fixed HNSW under L0.8 beside G2)."""
 
     def __init__(self, base: np.ndarray, g1: dict | None, g2: dict | None,
-                 traverse_dtype: str = "f32", metrics=U_HNSW):
+                 traverse_dtype: str = "f32", metrics=U_HNSW, base_p=(0.0, 0.0)):
         lib = load_library()
         base = np.ascontiguousarray(base, np.float32)
         self.n, self.d = base.shape
@@ -277,7 +289,9 @@ class Index:
         opts = _LoadOpts()
         opts.traverse_dtype = DTYPES[traverse_dtype]
         opts.base_metric[0], opts.base_metric[1] = int(metrics[0]), int(metrics[1])
+        opts.base_p[0], opts.base_p[1] = float(base_p[0]), float(base_p[1])
         self.metrics = tuple(metrics)
+        self.base_p = tuple(base_p)
         h = C.c_void_p(0)
         _check(lib.uhnsw_load(_np_ptr(base), self.n, self.d,
                               C.byref(s1) if s1 is not None else None,

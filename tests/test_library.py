@@ -121,6 +121,47 @@ def test_builder_l05_single_thread_equals_oracle(lib):
     assert _same_graph(go, gp)
 
 
+def test_builder_lp_single_thread_equals_oracle(lib):
+    """A graph under a general L_p (p = 0.8, metric 5) on 0/1 data, where every
+    |d_j|^0.8 is exactly 0 or 1: one-thread insertion reproduces the oracle's
+    FP64 construction under the same p exactly; p = 1 through the same entry
+    point is the L1 graph."""
+    r = np.random.default_rng(31)
+    base = r.integers(0, 2, size=(1500, 32)).astype(np.float32)
+    lv = I.hnsw_levels(len(base), 8, 5)
+    go = oracle.hnsw_build(base, None, 8, 30, lv, base_p=0.8)
+    gp = U.build_graph(base, U.BASE_LP, 8, 30, lv, threads=1, p=0.8)
+    assert _same_graph(go, gp)
+    g1 = U.build_graph(base, U.BASE_LP, 8, 30, lv, threads=1, p=1.0)
+    assert _same_graph(oracle.hnsw_build(base, 1, 8, 30, lv), g1)
+
+
+def test_lp_validation(lib):
+    """Base p outside (0, 2], an unknown metric code, or a first slot whose p
+    is not below the second's are refused before any device work."""
+    base = np.zeros((10, 4), np.float32)
+    lv = np.zeros(10, np.int32)
+    h = C.c_void_p(0)
+    for p in (0.0, -0.5, 2.5, float("nan")):
+        assert lib.uhnsw_build_graph_lp(base.ctypes.data, 10, 4, p, 4, 10, lv.ctypes.data, 1, 0,
+                                        C.byref(h)) == -1
+        assert b"outside" in lib.uhnsw_last_error()
+    g = {"num_levels": 1, "entry_point": 0, "max_degree0": 2, "max_degree": 2, "n": 4,
+         "levels": [{"nodes": np.arange(4, dtype=np.int32), "offsets": np.array([0, 1, 2, 3, 4]),
+                     "nbrs": np.array([1, 0, 3, 2], np.int32)}]}
+    s, keep = U._graph_struct(g)
+    b4 = np.zeros((4, 8), np.float32)
+    for metrics, bp, what in (((5, 2), (0.0, 0.0), b"outside"), ((5, 2), (2.5, 0.0), b"outside"),
+                              ((5, 5), (0.8, 0.8), b"below"), ((5, 1), (1.2, 0.0), b"below"),
+                              ((6, 2), (0.0, 0.0), b"uhnsw_base_metric")):
+        o = U._LoadOpts()
+        o.base_metric[0], o.base_metric[1] = metrics
+        o.base_p[0], o.base_p[1] = bp
+        assert lib.uhnsw_load(b4.ctypes.data, 4, 8, C.byref(s), C.byref(s), C.byref(o),
+                              C.byref(h)) == -1
+        assert what in lib.uhnsw_last_error(), (metrics, bp)
+
+
 def test_builder_parallel_invariants(lib):
     w, base, *_ = workload_arrays("sift1m", 8000, 4, 0.0, M=12, ef_construction=60)
     lv = I.graph_levels(w, 2)
