@@ -107,7 +107,11 @@ def test_gpu_build_validation(U):
     base = np.zeros((10, 4), np.float32)
     lv = np.zeros(10, np.int32)
     with pytest.raises(U.UHNSWError):
-        U.build_graph(base, 5, 4, 10, lv, device="gpu")
+        U.build_graph(base, 6, 4, 10, lv, device="gpu")
+    with pytest.raises(ValueError):
+        U.build_graph(base, U.BASE_LP, 4, 10, lv, device="gpu")     # L_p without its p
+    with pytest.raises(U.UHNSWError):
+        U.build_graph(base, U.BASE_LP, 4, 10, lv, device="gpu", p=2.5)
     with pytest.raises(U.UHNSWError):
         U.build_graph(base, 1, 4, 600, lv, device="gpu")       # efConstruction above 512
     lv[3] = -1
