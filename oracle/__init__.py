@@ -22,15 +22,18 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "uhnsw_oracle.c")
+_SRC_THREADS = os.path.join(_HERE, "batch_threads.c")
 _LIB = os.path.join(_HERE, "_uhnsw_oracle.so")
 _lib = None
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with the host C compiler (no SIMD flags, no fast-math)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_THREADS))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC,
+               _SRC_THREADS, "-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB)
     return _LIB
@@ -93,6 +96,11 @@ def _load():
     lib.oracle_uhnsw_query.argtypes = [C.POINTER(_CSR), C.POINTER(_CSR), C.c_int32, C.c_int32, P,
                                        C.c_int32, P, C.c_float, C.c_int32, C.c_int32, C.c_int32,
                                        C.c_float, C.c_int32, C.c_float, C.c_int32, P, P, P]
+    lib.oracle_uhnsw_batch_threads.restype = C.c_int
+    lib.oracle_uhnsw_batch_threads.argtypes = [C.POINTER(_CSR), C.POINTER(_CSR), C.c_int32,
+                                               C.c_int32, P, C.c_int32, P, P, C.c_int64,
+                                               C.c_int32, C.c_int32, C.c_int32, C.c_float,
+                                               C.c_int32, C.c_float, C.c_int32, C.c_int32, P, P]
     lib.oracle_uhnsw_query_p.restype = C.c_int
     lib.oracle_uhnsw_query_p.argtypes = [C.POINTER(_CSR), C.POINTER(_CSR), C.c_double, C.c_double,
                                          P, C.c_int32, P, C.c_float, C.c_int32, C.c_int32,
@@ -336,6 +344,28 @@ def uhnsw_batch(g1, g2, base, queries, p, k, ef, t=0, tau=0.92, kappa=0, cutoff=
         dist[i, :k[i]] = b
         stats[i] = s
     return ids, dist, stats
+
+
+def uhnsw_batch_threads(g1, g2, base, queries, p, k: int, ef: int, threads: int, t=0, tau=0.92,
+                        kappa=0, cutoff=1.4, mode=0, metrics=(1, 2), _holders=None):
+    """Algorithm 1 over a batch with one k and ef, the queries spread over
+    `threads` host threads (each query one single-threaded oracle call).
+    Returns ids int64 [nq, k] and dist float64 [nq, k]."""
+    base = _f32(base)
+    queries = _f32(queries)
+    nq = queries.shape[0]
+    p = _f32(np.broadcast_to(np.asarray(p, np.float32), (nq,)))
+    h1, h2 = _holders if _holders else (_CSRHolder(g1), _CSRHolder(g2))
+    ids = np.empty((nq, k), np.int64)
+    dist = np.empty((nq, k), np.float64)
+    rc = _load().oracle_uhnsw_batch_threads(C.byref(h1.s), C.byref(h2.s), int(metrics[0]),
+                                            int(metrics[1]), _ptr(base), base.shape[1],
+                                            _ptr(queries), _ptr(p), nq, k, ef, t, float(tau),
+                                            kappa, float(cutoff), mode, int(threads), _ptr(ids),
+                                            _ptr(dist))
+    if rc != 0:
+        raise ValueError(f"oracle_uhnsw_batch_threads: {rc}")
+    return ids, dist
 
 
 def recall(found_ids, true_ids, k=None) -> float:

@@ -544,3 +544,14 @@ def test_lp_graph_rejects_bad_p():
     for bp in (0.0, -1.0, 2.5):
         with pytest.raises(ValueError):
             oracle.hnsw_build(base, None, 2, 10, np.zeros(4, np.int32), base_p=bp)
+
+
+def test_threaded_batch_equals_query_loop(mixture_small):
+    """The multi-threaded batch driver (used to time the oracle on all host
+    cores) returns what the one-query loop returns, query for query."""
+    w, base, qs, p, g1, g2 = mixture_small
+    ids, dist, _ = oracle.uhnsw_batch(g1, g2, base, qs, p, 10, 32)
+    for threads in (1, 3, 8):
+        ti, td = oracle.uhnsw_batch_threads(g1, g2, base, qs, p, 10, 32, threads)
+        np.testing.assert_array_equal(ti, ids)
+        np.testing.assert_array_equal(td, dist)
