@@ -236,22 +236,62 @@ def run_ours(args, log):
         "fp16_batched": dict(index=idx16, opts=dict(persistent=True, use_graph=True, **qt)),
     }
     forms = {k_: v for k_, v in forms.items() if k_ in args.forms.split(",")}
-    # calibration (untimed): smallest ef meeting the recall target in every p bin
-    for name, f in forms.items():
-        f["ef"], f["recall"], f["recall_min_bin"] = None, None, None
-        for ef in EF_SWEEP:
-            with torch.cuda.stream(stream):
-                ids, _, _ = f["index"].search(q_dev, p_dev, k=k, ef=ef, stream=stream, **f["opts"])
-            torch.cuda.synchronize()
-            r, per = recall_per_bin(ids.cpu().numpy(), gt, p, k)
-            f["ef"], f["recall"], f["recall_min_bin"] = ef, r, min(per.values())
-            if min(per.values()) >= RECALL_TARGET:
-                break
-        log(f"{name}: ef={f['ef']} recall={f['recall']:.4f} min-bin={f['recall_min_bin']:.4f}")
-
     flush = torch.empty(384 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     out_ids = torch.empty((w.nq, k), dtype=torch.int64, device="cuda")
     out_d = torch.empty((w.nq, k), dtype=torch.float32, device="cuda")
+
+    def calibrate(f, opts):
+        """Smallest ef meeting the recall target in every p bin (untimed);
+        with --ef, that beam alone (its recall still measured)."""
+        out = None
+        for ef in ([args.ef] if args.ef else EF_SWEEP):
+            with torch.cuda.stream(stream):
+                ids, _, _ = f["index"].search(q_dev, p_dev, k=k, ef=ef, stream=stream, **opts)
+            torch.cuda.synchronize()
+            r, per = recall_per_bin(ids.cpu().numpy(), gt, p, k)
+            out = (ef, r, min(per.values()))
+            if out[2] >= RECALL_TARGET:
+                break
+        return out
+
+    def quick_ms(f, ef, opts, steps=10):
+        """Median device time of a few L2-flushed calls (untimed selection)."""
+        ms = []
+        for i in range(3 + steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+                a.record(stream)
+                f["index"].search(q_dev, p_dev, k=k, ef=ef, stream=stream, out=(out_ids, out_d),
+                                  **opts)
+                b.record(stream)
+            torch.cuda.synchronize()
+            if i >= 3:
+                ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    # Calibration.  The plain form runs HNSW's own order (one expansion per
+    # step, the deterministic mode).  The batched form may expand the first
+    # `width` unexpanded beam entries per step (the fast mode): each width in
+    # the sweep gets its smallest ef meeting the recall target, and the
+    # fastest pair is kept.  Recall is measured, never assumed.
+    widths = [int(x) for x in args.widths.split(",")]
+    for name, f in forms.items():
+        f["calibration"] = []
+        for width in (widths if name == "fp16_batched" else [1]):
+            opts = dict(f["opts"], width=width)
+            ef, r, rmin = calibrate(f, opts)
+            ms = quick_ms(f, ef, opts) if name == "fp16_batched" and len(widths) > 1 else None
+            f["calibration"].append({"width": width, "ef": ef, "recall_at_10": round(r, 4),
+                                     "recall_at_10_min_p_bin": round(rmin, 4),
+                                     "ms": None if ms is None else round(ms, 4)})
+            log(f"{name}: width={width} ef={ef} recall={r:.4f} min-bin={rmin:.4f}"
+                + ("" if ms is None else f" {ms:.4f} ms"))
+        ok = [c for c in f["calibration"] if c["recall_at_10_min_p_bin"] >= RECALL_TARGET]
+        best = min(ok or f["calibration"], key=lambda c: (c["ms"] or 0.0, c["width"]))
+        f["width"], f["ef"] = best["width"], best["ef"]
+        f["recall"], f["recall_min_bin"] = best["recall_at_10"], best["recall_at_10_min_p_bin"]
+        f["opts"] = dict(f["opts"], width=f["width"])
 
     def time_form(f, steps, warmup):
         call = lambda: f["index"].search(q_dev, p_dev, k=k, ef=f["ef"], stream=stream,
@@ -301,7 +341,8 @@ def run_ours(args, log):
             kern_ms.append(kev[0].elapsed_time(kev[1]))
 
     # algorithmic bytes of one launch (counted by the kernel's own counters)
-    _, _, st = head["index"].search(q_dev, p_dev, k=k, ef=head["ef"], stats=True, **qt)
+    _, _, st = head["index"].search(q_dev, p_dev, k=k, ef=head["ef"], stats=True,
+                                    width=head["width"], **qt)
     st = st.cpu().numpy().astype(np.int64)
     row16, row32 = w.d * 2, w.d * 4
     deg0 = g1["max_degree0"]
@@ -320,7 +361,8 @@ def run_ours(args, log):
     if os.path.exists(prof):
         try:
             pj = json.load(open(prof))
-            if pj.get("source_sha") == _source_sha():
+            if (pj.get("source_sha") == _source_sha() and pj.get("ef") == head["ef"]
+                    and pj.get("search_width") == head["width"]):
                 traffic = pj.get("dram_bytes_per_launch")
         except (OSError, ValueError):
             pass
@@ -330,7 +372,7 @@ def run_ours(args, log):
     pin_p = torch.from_numpy(p).pin_memory().numpy()
     pin_ids = torch.empty((w.nq, k), dtype=torch.int64).pin_memory().numpy()
     pin_d = torch.empty((w.nq, k), dtype=torch.float32).pin_memory().numpy()
-    e2e_opts = dict(persistent=True, **qt)
+    e2e_opts = dict(persistent=True, width=head["width"], **qt)
     for _ in range(args.warmup):
         head["index"].search_host(pin_q, pin_p, k=k, ef=head["ef"], out=(pin_ids, pin_d),
                                   stream=stream, **e2e_opts)
@@ -354,11 +396,13 @@ def run_ours(args, log):
             # untimed warm-up: a server of its own replays the first 1,000
             # requests, so that first-launch costs stay out of the latencies
             warm = U.Server(head["index"], max_batch=256, streams=4, k_max=k,
-                            ef_max=max(head["ef"], k), max_delay_us=100, **qt)
+                            ef_max=max(head["ef"], k), max_delay_us=100, width=head["width"],
+                            **qt)
             warm.replay(qs[:1000], p[:1000], k, head["ef"], arr[:1000])
             warm.close()
             srv = U.Server(head["index"], max_batch=256, streams=4, k_max=k,
-                           ef_max=max(head["ef"], k), max_delay_us=100, **qt)
+                           ef_max=max(head["ef"], k), max_delay_us=100, width=head["width"],
+                           **qt)
             s_ids, _, lat = srv.replay(qs, p, k, head["ef"], arr)
             sst = srv.stats()
             srv.close()
@@ -385,7 +429,9 @@ def run_ours(args, log):
             "form": "fp16_batched: FP16 traversal rows, FP32 verification, persistent launch, "
                     "CUDA-graph replay",
             "kernel": "warp per query" if args.query_threads != 128 else "block per query",
-            "ef": head["ef"], "t": "ef", "verify": "exact with partial-sum abandon",
+            "ef": head["ef"], "search_width": head["width"], "t": "ef",
+            "verify": "exact with partial-sum abandon",
+            "calibration": head["calibration"],
             "recall_at_10": round(head["recall"], 4),
             "recall_at_10_min_p_bin": round(head["recall_min_bin"], 4),
             "l2": "flushed (384 MB write) between timed steps",
@@ -393,6 +439,7 @@ def run_ours(args, log):
                 forms["plain_fp32"]["ms"]), 1), "ef": forms["plain_fp32"]["ef"],
                 "recall_at_10": round(forms["plain_fp32"]["recall"], 4),
                 "recall_at_10_min_p_bin": round(forms["plain_fp32"]["recall_min_bin"], 4),
+                "search_width": 1,
                 "ms_per_step": round(statistics.mean(forms["plain_fp32"]["ms"]), 4)}
                 if "plain_fp32" in forms else None),
             "stats_per_query": {"N_b": float(st[:, 0].mean()), "N_p": float(st[:, 1].mean()),
@@ -417,7 +464,10 @@ def run_ours(args, log):
         "serving": serving,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, base, qs, p, g1, g2, head["ef"], k, args.cpu_seconds)
+        # the oracle runs HNSW's own order: its operating point is the
+        # width-1 calibration's ef
+        ef1 = next((c["ef"] for c in head["calibration"] if c["width"] == 1), head["ef"])
+        line["cpu_baseline"] = cpu_baseline(w, base, qs, p, g1, g2, ef1, k, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if idx32 is not None:
@@ -1017,6 +1067,11 @@ def main():
                     help="oracle-arm queries per step and host core")
     ap.add_argument("--forms", default="plain_fp32,fp16_batched",
                     help="comma-separated subset of the forms to run (the JSON line needs fp16_batched)")
+    ap.add_argument("--ef", type=int, default=0,
+                    help="fixed beam instead of the calibration sweep (profiling runs)")
+    ap.add_argument("--widths", default="1,2,3",
+                    help="search widths the batched form calibrates (beam entries expanded per "
+                         "step; 1 = HNSW's own order)")
     ap.add_argument("--query-threads", type=int, default=32, choices=(32, 128),
                     help="32: warp-per-query kernel, 128: block-per-query kernel")
     ap.add_argument("--workload", default="sift1m",

@@ -86,6 +86,9 @@ def _load():
     lib.oracle_hnsw_search_p.restype = C.c_int
     lib.oracle_hnsw_search_p.argtypes = [C.POINTER(_CSR), P, C.c_int32, C.c_double, P, C.c_int32,
                                          C.c_int32, P, P, P]
+    lib.oracle_hnsw_search_w.restype = C.c_int
+    lib.oracle_hnsw_search_w.argtypes = [C.POINTER(_CSR), P, C.c_int32, C.c_double, P, C.c_int32,
+                                         C.c_int32, C.c_int32, P, P, P]
     lib.oracle_verify_exact.restype = C.c_int
     lib.oracle_verify_exact.argtypes = [P, C.c_int32, P, C.c_double, P, C.c_int32, C.c_int32,
                                         C.c_int32, P, P, P]
@@ -101,6 +104,11 @@ def _load():
                                                C.c_int32, P, C.c_int32, P, P, C.c_int64,
                                                C.c_int32, C.c_int32, C.c_int32, C.c_float,
                                                C.c_int32, C.c_float, C.c_int32, C.c_int32, P, P]
+    lib.oracle_uhnsw_query_w.restype = C.c_int
+    lib.oracle_uhnsw_query_w.argtypes = [C.POINTER(_CSR), C.POINTER(_CSR), C.c_double, C.c_double,
+                                         P, C.c_int32, P, C.c_float, C.c_int32, C.c_int32,
+                                         C.c_int32, C.c_float, C.c_int32, C.c_float, C.c_int32,
+                                         C.c_int32, P, P, P]
     lib.oracle_uhnsw_query_p.restype = C.c_int
     lib.oracle_uhnsw_query_p.argtypes = [C.POINTER(_CSR), C.POINTER(_CSR), C.c_double, C.c_double,
                                          P, C.c_int32, P, C.c_float, C.c_int32, C.c_int32,
@@ -242,16 +250,23 @@ class _CSRHolder:
 
 
 # ---------------------------------------------------------------- O3
-def hnsw_search(graph, base, q, metric: int | None, ef: int, t: int, base_p: float | None = None):
+def hnsw_search(graph, base, q, metric: int | None, ef: int, t: int, base_p: float | None = None,
+                width: int | None = None):
     """KnnSearch(q, t) with beam ef on a CSR graph (base metric by code, or
     L_base_p when metric is None): (ids int64 [t], base dist float64 [t],
-    number of base-distance evaluations)."""
+    number of base-distance evaluations).  With `width` given, the layer-0
+    beam expands that many entries per step (the GPU's fast mode; width = 1
+    is HNSW's order through a second, independent routine)."""
     base, q = _f32(base), _f32(q)
     h = _CSRHolder(graph)
     ids = np.empty(t, np.int64)
     dd = np.empty(t, np.float64)
     nd = C.c_int64(0)
-    if metric is None:
+    if width is not None:
+        bp = _bp(base_p) if metric is None else METRIC_P[int(metric)]
+        rc = _load().oracle_hnsw_search_w(C.byref(h.s), _ptr(base), base.shape[1], bp, _ptr(q),
+                                          ef, t, int(width), _ptr(ids), _ptr(dd), C.byref(nd))
+    elif metric is None:
         rc = _load().oracle_hnsw_search_p(C.byref(h.s), _ptr(base), base.shape[1], _bp(base_p),
                                           _ptr(q), ef, t, _ptr(ids), _ptr(dd), C.byref(nd))
     else:
@@ -296,19 +311,27 @@ def verify_paper(base, q, p: float, cand, k: int, kappa: int, tau: float):
 # ---------------------------------------------------------------- Algorithm 1
 def uhnsw_query(g1, g2, base, q, p: float, k: int, ef: int, t: int = 0, tau: float = 0.92,
                 kappa: int = 0, cutoff: float = 1.4, mode: int = 0, metrics=(1, 2), _holders=None,
-                base_p=None):
+                base_p=None, width: int = 1):
     """One query of Algorithm 1: (ids int64 [k], dist float64 [k], stats [N_b, N_p, terms]).
     g1 / g2 are the graphs routed for p <= cutoff / p > cutoff, under the base
     metrics `metrics` (U-HNSW: (1, 2); U-HNSW-E: (3, 1) with cutoff 0.6), or,
     when base_p = (pa, pb) is given, under L_pa and L_pb (a fixed HNSW at p:
-    the same L_p graph in both slots, base_p = (p, p))."""
+    the same L_p graph in both slots, base_p = (p, p)).  width > 1 runs
+    the layer-0 beam in the GPU's fast mode (that many expansions per step)."""
     base, q = _f32(base), _f32(q)
     h1 = _holders[0] if _holders else _CSRHolder(g1)
     h2 = _holders[1] if _holders else _CSRHolder(g2)
     ids = np.empty(k, np.int64)
     dist = np.empty(k, np.float64)
     st = np.zeros(3, np.int64)
-    if base_p is not None:
+    if width != 1:
+        bpa, bpb = ((_bp(base_p[0]), _bp(base_p[1])) if base_p is not None
+                    else (METRIC_P[int(metrics[0])], METRIC_P[int(metrics[1])]))
+        rc = _load().oracle_uhnsw_query_w(C.byref(h1.s), C.byref(h2.s), bpa, bpb, _ptr(base),
+                                          base.shape[1], _ptr(q), float(p), k, ef, t, float(tau),
+                                          kappa, float(cutoff), mode, int(width), _ptr(ids),
+                                          _ptr(dist), _ptr(st))
+    elif base_p is not None:
         rc = _load().oracle_uhnsw_query_p(C.byref(h1.s), C.byref(h2.s), _bp(base_p[0]),
                                           _bp(base_p[1]), _ptr(base), base.shape[1], _ptr(q),
                                           float(p), k, ef, t, float(tau), kappa, float(cutoff),
@@ -324,7 +347,7 @@ def uhnsw_query(g1, g2, base, q, p: float, k: int, ef: int, t: int = 0, tau: flo
 
 
 def uhnsw_batch(g1, g2, base, queries, p, k, ef, t=0, tau=0.92, kappa=0, cutoff=1.4, mode=0,
-                metrics=(1, 2), base_p=None):
+                metrics=(1, 2), base_p=None, width=1):
     """Algorithm 1 over a batch (per-query p, k, ef arrays or scalars).
     Returns ids int64 [nq, kmax] and dist float64 [nq, kmax] (-1 / inf padded)."""
     queries = _f32(queries)
@@ -339,7 +362,8 @@ def uhnsw_batch(g1, g2, base, queries, p, k, ef, t=0, tau=0.92, kappa=0, cutoff=
     stats = np.zeros((nq, 3), np.int64)
     for i in range(nq):
         a, b, s = uhnsw_query(g1, g2, base, queries[i], float(p[i]), int(k[i]), int(ef[i]), t, tau,
-                              kappa, cutoff, mode, metrics, _holders=holders, base_p=base_p)
+                              kappa, cutoff, mode, metrics, _holders=holders, base_p=base_p,
+                              width=width)
         ids[i, :k[i]] = a
         dist[i, :k[i]] = b
         stats[i] = s

@@ -30,13 +30,17 @@
  *                         sum exceeds the running K-th best sum
  *   oracle_verify_paper   Algorithm 1, lines 6-10: batches of kappa with the
  *                         |R_new ∩ R| / K >= tau early stop (Section 3.1)
+ *   oracle_hnsw_search_w  KnnSearch whose layer-0 beam expands `width`
+ *                         entries per step: the GPU's fast mode, a GPU
+ *                         adaptation (width = 1 is HNSW's own order)
  *   oracle_uhnsw_query    Algorithm 1 end to end, with the p <= cutoff
  *                         routing (Section 3.1) and the direct K-NN for
  *                         p in {1, 2} (Section 3 introduction); with graphs
  *                         under L0.5 and L1 and cutoff 0.6 it is U-HNSW-E
  *                         (Section 4.6), whose direct K-NN is for p in
  *                         {0.5, 1}; oracle_uhnsw_query_p takes the two
- *                         graphs' p instead of metric codes
+ *                         graphs' p instead of metric codes, and
+ *                         oracle_uhnsw_query_w a search width as well
  *
  * Order used everywhere: lexicographic (distance, id), ids ascending on ties.
  * Base metrics (metric codes): 1 = L1, sum |d_j|; 2 = the squared L2 sum
@@ -316,6 +320,71 @@ static int search_layer(const gview_t* g, const float* base, int32_t d, double b
   return 1;
 }
 
+/*
+ * Layer search that expands `width` beam entries per step.  This is a GPU
+ * adaptation, not the paper's search: with width = 1 it is HNSW's own order
+ * (SEARCH-LAYER above expands the nearest unexpanded entry of W, and stops
+ * when every entry of W is expanded), and with width > 1 a step takes
+ * several parents before their neighbours are ranked:
+ *   W <- ep (every entry unexpanded); v <- ep
+ *   repeat:
+ *     P <- the first `width` unexpanded entries of W, in W's order, now expanded
+ *     if P is empty: stop
+ *     N <- the neighbours at layer lc of each parent in P's order, in list
+ *          order, that are not in v (each joins v as it is taken)
+ *     W <- the ef nearest of W + N by (distance, id); entries of N unexpanded
+ * W is kept sorted ascending with an expanded flag per entry.
+ */
+static int search_layer_wide(const gview_t* g, const float* base, int32_t d, double bp,
+                             const float* q, int64_t ep, double ep_d, int32_t ef, int32_t width,
+                             int32_t lc, visited_t* vis, pset_t* W, int64_t* n_dist) {
+  visited_next(vis);
+  if (!pset_grow(W, ef + 1)) return 0;
+  unsigned char* ex = (unsigned char*)calloc((size_t)ef + 1, 1);
+  int64_t* par = (int64_t*)malloc(sizeof(int64_t) * (size_t)width);
+  if (!ex || !par) { free(ex); free(par); return 0; }
+  W->cnt = 1;
+  W->d[0] = ep_d;
+  W->id[0] = ep;
+  vis->mark[ep] = vis->gen;
+  for (;;) {
+    int32_t np = 0;
+    for (int32_t i = 0; i < W->cnt && np < width; ++i)
+      if (!ex[i]) { ex[i] = 1; par[np++] = W->id[i]; }
+    if (np == 0) break;
+    for (int32_t j = 0; j < np; ++j) {
+      const int32_t* nb;
+      int32_t nn;
+      neighbours(g, (int32_t)par[j], lc, &nb, &nn);
+      for (int32_t a = 0; a < nn; ++a) {
+        int64_t e = nb[a];
+        if (e < 0 || vis->mark[e] == vis->gen) continue;
+        vis->mark[e] = vis->gen;
+        double de = base_dist_p(base + e * (int64_t)d, q, d, bp);
+        if (n_dist) (*n_dist)++;
+        /* W <- the ef nearest of W + {e}, e unexpanded (the order in which the
+         * step's candidates are added does not change the resulting set) */
+        int32_t c = W->cnt;
+        if (c == ef && !pair_less(de, e, W->d[c - 1], W->id[c - 1])) continue;
+        int32_t pos = (c == ef) ? c - 1 : c;
+        while (pos > 0 && pair_less(de, e, W->d[pos - 1], W->id[pos - 1])) {
+          W->d[pos] = W->d[pos - 1];
+          W->id[pos] = W->id[pos - 1];
+          ex[pos] = ex[pos - 1];
+          --pos;
+        }
+        W->d[pos] = de;
+        W->id[pos] = e;
+        ex[pos] = 0;
+        if (c < ef) W->cnt = c + 1;
+      }
+    }
+  }
+  free(ex);
+  free(par);
+  return 1;
+}
+
 /* ------------------------------------------------------------------ */
 /* SELECT-NEIGHBORS-HEURISTIC (HNSW Algorithm 4; no candidate          */
 /* extension, pruned connections not kept)                             */
@@ -578,6 +647,44 @@ int oracle_hnsw_search(const oracle_csr* g, const float* base, int32_t d, int32_
   return oracle_hnsw_search_p(g, base, d, metric_p(metric), q, ef, t, out_ids, out_d, n_dist);
 }
 
+/*
+ * KnnSearch with the layer-0 beam expanding `width` entries per step (the
+ * GPU's fast mode, search_layer_wide): the upper levels as in
+ * oracle_hnsw_search_p (beam 1), then layer 0 by search_layer_wide.  With
+ * width = 1 it returns what oracle_hnsw_search_p returns.
+ */
+int oracle_hnsw_search_w(const oracle_csr* g, const float* base, int32_t d, double bp,
+                         const float* q, int32_t ef, int32_t t, int32_t width, int64_t* out_ids,
+                         double* out_d, int64_t* n_dist) {
+  if (ef < 1 || t < 1 || width < 1 || !valid_bp(bp)) return OR_EINVAL;
+  gview_t view = {NULL, NULL, g};
+  visited_t vis = {(uint32_t*)calloc(g->n, sizeof(uint32_t)), 0, g->n};
+  pset_t W = {0};
+  if (!vis.mark) return OR_ENOMEM;
+  int64_t ep = g->entry_point;
+  double epd = base_dist_p(base + ep * (int64_t)d, q, d, bp);
+  if (n_dist) (*n_dist)++;
+  int ok = 1;
+  for (int32_t lc = g->num_levels - 1; lc >= 1 && ok; --lc) {
+    ok = search_layer(&view, base, d, bp, q, &ep, &epd, 1, 1, lc, &vis, &W, n_dist);
+    if (ok) {
+      ep = W.id[0];
+      epd = W.d[0];
+    }
+  }
+  if (ok) ok = search_layer_wide(&view, base, d, bp, q, ep, epd, ef, width, 0, &vis, &W, n_dist);
+  if (ok) {
+    for (int32_t i = 0; i < t; ++i) {
+      out_ids[i] = i < W.cnt ? W.id[i] : -1;
+      out_d[i] = i < W.cnt ? W.d[i] : INFINITY;
+    }
+  }
+  free(vis.mark);
+  free(W.d);
+  free(W.id);
+  return ok ? OR_OK : OR_ENOMEM;
+}
+
 /* ------------------------------------------------------------------ */
 /* O4: verification of a candidate set (Section 3.1)                   */
 /* ------------------------------------------------------------------ */
@@ -691,11 +798,12 @@ int oracle_verify_paper(const float* base, int32_t d, const float* q, double p, 
  * evaluations (N_b), stats[1] = L_p candidates computed (N_p), stats[2] = L_p
  * terms.
  */
-int oracle_uhnsw_query_p(const oracle_csr* ga, const oracle_csr* gb, double bpa, double bpb,
+int oracle_uhnsw_query_w(const oracle_csr* ga, const oracle_csr* gb, double bpa, double bpb,
                          const float* base, int32_t d, const float* q, float p, int32_t k,
                          int32_t ef, int32_t t, float tau, int32_t kappa, float cutoff,
-                         int32_t mode, int64_t* out_ids, double* out_dist, int64_t* stats) {
-  if (k < 1 || ef < 1 || !(p > 0.0f) || !(p <= 2.0f)) return OR_EINVAL;
+                         int32_t mode, int32_t width, int64_t* out_ids, double* out_dist,
+                         int64_t* stats) {
+  if (k < 1 || ef < 1 || width < 1 || !(p > 0.0f) || !(p <= 2.0f)) return OR_EINVAL;
   if (!valid_bp(bpa) || !valid_bp(bpb)) return OR_EINVAL;
   int64_t nb = 0, np = 0, nterm = 0;
   const float pa = (float)bpa, pb = (float)bpb;
@@ -711,7 +819,8 @@ int oracle_uhnsw_query_p(const oracle_csr* ga, const oracle_csr* gb, double bpa,
   int32_t* C32 = (int32_t*)malloc(sizeof(int32_t) * tt);
   double* S = (double*)malloc(sizeof(double) * k);
   if (!C || !Cd || !C32 || !S) { free(C); free(Cd); free(C32); free(S); return OR_ENOMEM; }
-  int rc = oracle_hnsw_search_p(g, base, d, bp, q, efp, tt, C, Cd, &nb);
+  int rc = width == 1 ? oracle_hnsw_search_p(g, base, d, bp, q, efp, tt, C, Cd, &nb)
+                      : oracle_hnsw_search_w(g, base, d, bp, q, efp, tt, width, C, Cd, &nb);
   if (rc != OR_OK) { free(C); free(Cd); free(C32); free(S); return rc; }
   if (direct) {
     for (int32_t j = 0; j < k; ++j) {
@@ -734,6 +843,14 @@ int oracle_uhnsw_query_p(const oracle_csr* ga, const oracle_csr* gb, double bpa,
   if (stats) { stats[0] = nb; stats[1] = np; stats[2] = nterm; }
   free(C); free(Cd); free(C32); free(S);
   return OR_OK;
+}
+
+int oracle_uhnsw_query_p(const oracle_csr* ga, const oracle_csr* gb, double bpa, double bpb,
+                         const float* base, int32_t d, const float* q, float p, int32_t k,
+                         int32_t ef, int32_t t, float tau, int32_t kappa, float cutoff,
+                         int32_t mode, int64_t* out_ids, double* out_dist, int64_t* stats) {
+  return oracle_uhnsw_query_w(ga, gb, bpa, bpb, base, d, q, p, k, ef, t, tau, kappa, cutoff, mode,
+                              1, out_ids, out_dist, stats);
 }
 
 int oracle_uhnsw_query(const oracle_csr* ga, const oracle_csr* gb, int32_t ma, int32_t mb,

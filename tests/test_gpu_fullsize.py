@@ -1,9 +1,11 @@
 """Parity at the bench's full size: 1,000,000 x 128 SIFT-shaped rows, 10,000
 queries, the FP16 batched form (persistent launch, CUDA-graph replay, warp
-per query) at the operating point ef = 48.  The oracle computes sampled
-outputs one by one on the same graphs: its Algorithm 1 result (the FP16
-copy of integer data is exact, so the beam is the oracle's and only L_p
-near-ties may differ) and its exact top-10 for the recall spot check."""
+per query) at the operating points the bench calibrates: ef = 48 with one
+expansion per step, and the fast mode's widths 2 and 3 at ef = 40 and 48.
+The oracle computes sampled outputs one by one on the same graphs: its
+Algorithm 1 result at the same width (the FP16 copy of integer data is
+exact, so the beam is the oracle's and only L_p near-ties may differ) and
+its exact top-10 for the recall spot check."""
 import os
 
 import numpy as np
@@ -60,3 +62,25 @@ def test_full_size_sampled_parity(full):
     gt, _ = oracle.exact_knn(base, qs[few], p[few], 10)
     hits = sum(len(set(ids[i].tolist()) & set(gt[j].tolist())) for j, i in enumerate(few))
     assert hits / (10 * len(few)) >= 0.9
+
+
+@pytest.mark.parametrize("width,ef", [(2, 40), (3, 40), (2, 48)])
+def test_full_size_fast_mode_sampled_parity(full, width, ef):
+    U, w, base, qs, p, g1, g2, idx = full
+    q, pp = torch.from_numpy(qs).cuda(), torch.from_numpy(p).cuda()
+    ids, dist, st = idx.search(q, pp, k=10, ef=ef, width=width, persistent=True, use_graph=True,
+                               stats=True)
+    ids2, dist2, _ = idx.search(q, pp, k=10, ef=ef, width=width, persistent=True, use_graph=True)
+    torch.cuda.synchronize()
+    assert idx.device_status() == 0
+    ids, dist, st = ids.cpu().numpy(), dist.cpu().numpy(), st.cpu().numpy()
+    assert np.array_equal(ids, ids2.cpu().numpy()) and np.array_equal(dist, dist2.cpu().numpy())
+    assert (st[:, 5] == 0).all()
+    holders = (oracle._CSRHolder(g1), oracle._CSRHolder(g2))
+    sample = np.random.default_rng(1).choice(len(qs), size=16, replace=False)
+    sample[:2] = [int(np.argmax(p == 1.0)), int(np.argmax(p == 2.0))]
+    for i in sample:
+        rid, rd, rst = oracle.uhnsw_query(g1, g2, base, qs[i], float(p[i]), 10, ef,
+                                          _holders=holders, width=width)
+        check_topk(base, qs[i], p[i], ids[i], dist[i], rid, 10,
+                   f"query {i} p={p[i]} width={width}")

@@ -555,3 +555,60 @@ def test_threaded_batch_equals_query_loop(mixture_small):
         ti, td = oracle.uhnsw_batch_threads(g1, g2, base, qs, p, 10, 32, threads)
         np.testing.assert_array_equal(ti, ids)
         np.testing.assert_array_equal(td, dist)
+
+
+# ----------------------------------------------------------------- several expansions per step
+def _csr1(lists, entry=0):
+    n = len(lists)
+    offs = np.zeros(n + 1, np.int64)
+    offs[1:] = np.cumsum([len(l) for l in lists])
+    nbrs = np.array([v for l in lists for v in l], np.int32)
+    return {"num_levels": 1, "entry_point": entry, "max_degree0": 4, "max_degree": 2, "n": n,
+            "levels": [{"nodes": np.arange(n, dtype=np.int32), "offsets": offs, "nbrs": nbrs}]}
+
+
+def test_wide_search_by_hand():
+    """Points on a line, query at 0: E=10 (entry), A=5, B=6, C=2 (a neighbour
+    of A), D=1 (a neighbour of B); ef = 2.  One expansion per step expands A
+    first, C then pushes B out of W before B is expanded: W = [C, A].  Two per
+    step expand A and B together, so D enters: W = [D, C]."""
+    base = np.array([[10.0], [5.0], [6.0], [2.0], [1.0]], np.float32)
+    g = _csr1([[1, 2], [0, 3], [0, 4], [1], [2]])
+    q = np.zeros(1, np.float32)
+    for width in (None, 1):
+        ids, dd, nd = oracle.hnsw_search(g, base, q, 1, ef=2, t=2, width=width)
+        assert ids.tolist() == [3, 1] and dd.tolist() == [2.0, 5.0] and nd == 4
+    ids, dd, nd = oracle.hnsw_search(g, base, q, 1, ef=2, t=2, width=2)
+    assert ids.tolist() == [4, 3] and dd.tolist() == [1.0, 2.0] and nd == 5
+
+
+def test_wide_search_width1_equals_hnsw(mixture_small):
+    """The width-w routine at width 1 and HNSW's SEARCH-LAYER are written
+    independently; they agree id for id and distance for distance."""
+    w, base, qs, p, g1, g2 = mixture_small
+    for metric, g in ((1, g1), (2, g2)):
+        for ef in (4, 24, 64):
+            for i in range(10):
+                a = oracle.hnsw_search(g, base, qs[i], metric, ef=ef, t=ef)
+                b = oracle.hnsw_search(g, base, qs[i], metric, ef=ef, t=ef, width=1)
+                np.testing.assert_array_equal(a[0], b[0])
+                np.testing.assert_array_equal(a[1], b[1])
+                assert a[2] == b[2]
+
+
+@pytest.mark.parametrize("width", [2, 3, 8])
+def test_wide_search_full_beam_is_exact(mixture_small, width):
+    """With ef >= N every node of the connected layer 0 is reached whatever
+    the width, so the first t results are the exact base-metric top-t, and
+    Algorithm 1 with t = ef = N equals the exact L_p answer."""
+    w, base, qs, p, g1, g2 = mixture_small
+    n = len(base)
+    D = cdist(qs[:3].astype(np.float64), base.astype(np.float64), "cityblock")
+    for i in range(3):
+        ids, dd, nd = oracle.hnsw_search(g1, base, qs[i], 1, ef=n, t=20, width=width)
+        order = np.lexsort((np.arange(n), D[i]))[:20]
+        np.testing.assert_array_equal(ids, order)
+        assert nd >= n
+    gt, _ = oracle.exact_knn(base, qs[:3], p[:3], 10)
+    ids, _, _ = oracle.uhnsw_batch(g1, g2, base, qs[:3], p[:3], 10, n, t=n, width=width)
+    np.testing.assert_array_equal(ids, gt)
