@@ -7,9 +7,11 @@ tests, ``__graft_entry__.smoke()`` and the bench's CPU-baseline leg may use
 this package; the library under ``paper_2605_02030_gb300`` never imports it.
 
 Pinned by ``tests/test_oracle.py`` (closed forms, library routines, hand-
-derived graphs, invariants).  ``hnsw_build`` is "parity unpinned" beyond the
-hand-derived small graphs: its output is an index whose quality is checked
-(connectivity, degree bounds, search recall), not compared with a reference.
+derived graphs, invariants).  ``hnsw_build`` is pinned by hand-derived small
+graphs and, at efConstruction >= N, by a brute-force insertion (every
+reachable earlier node ranked); at smaller efConstruction its graph follows
+the insertion beam, whose search is pinned on its own, and the index quality
+is checked (connectivity, degree bounds, search recall).
 """
 from __future__ import annotations
 

@@ -17,8 +17,10 @@
  *   oracle_hnsw_build     HNSW construction under L1 (G1) or L2 (G2)
  *                         (Section 2.2; the published HNSW insertion,
  *                         Malkov & Yashunin, Algorithms 1, 2 and 4).
- *                         PARITY UNPINNED beyond hand-derived small graphs:
- *                         graph quality is checked, not an exact reference.
+ *                         Pinned by hand-derived graphs and, at
+ *                         efConstruction >= N, by brute-force insertion
+ *                         (every reachable earlier node ranked); below that
+ *                         the graph follows the beam, pinned on its own.
  *   oracle_hnsw_build_p   the same construction under any L_bp, 0 < bp <= 2
  *                         (the fixed-p HNSW of Section 4.3, one graph per p)
  *   oracle_hnsw_search    KnnSearch(q, t) on a CSR graph (Section 2.2 and

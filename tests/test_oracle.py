@@ -612,3 +612,87 @@ def test_wide_search_full_beam_is_exact(mixture_small, width):
     gt, _ = oracle.exact_knn(base, qs[:3], p[:3], 10)
     ids, _, _ = oracle.uhnsw_batch(g1, g2, base, qs[:3], p[:3], 10, n, t=n, width=width)
     np.testing.assert_array_equal(ids, gt)
+
+
+# ----------------------------------------------------------------- construction by brute force
+def _brute_build(base, levels, M, M0, metric, reach_from_entry):
+    """HNSW insertion with the insertion beam replaced by brute force: at
+    each level the candidates of a new node are all earlier nodes on that
+    level (or, with reach_from_entry, those reachable from node 0 in the
+    current single-layer graph), ranked by (distance, id); the neighbour
+    heuristic keeps a candidate only if it is strictly nearer to the new node
+    than to every neighbour already kept; reverse links overflowing their cap
+    are re-selected by the same heuristic.  Integer data keeps every sum
+    exact, so the ranking is the oracle's."""
+    X = base.astype(np.float64)
+
+    def dist(a, b):
+        diff = X[a] - X[b]
+        return float(np.abs(diff).sum()) if metric == 1 else float((diff * diff).sum())
+
+    def heuristic(cand, m, b):
+        out = []
+        for dc, c in cand:
+            if len(out) >= m:
+                break
+            if all(dc < dist(c, r) for r in out):
+                out.append(c)
+        return out
+
+    n = len(base)
+    links = [[[] for _ in range(levels[v] + 1)] for v in range(n)]
+    for q in range(1, n):
+        L = int(levels[:q].max())
+        for lc in range(min(L, int(levels[q])), -1, -1):
+            pool = [v for v in range(q) if levels[v] >= lc]
+            if reach_from_entry:
+                seen, stack = {0}, [0]
+                while stack:
+                    u = stack.pop()
+                    for x in links[u][lc]:
+                        if x not in seen:
+                            seen.add(x)
+                            stack.append(x)
+                pool = [v for v in pool if v in seen]
+            cand = sorted((dist(q, v), v) for v in pool)
+            sel = heuristic(cand, M, q)
+            links[q][lc] = sel
+            cap = M0 if lc == 0 else M
+            for e in sel:
+                links[e][lc].append(q)
+                if len(links[e][lc]) > cap:
+                    c2 = sorted((dist(e, v), v) for v in links[e][lc])
+                    links[e][lc] = heuristic(c2, cap, e)
+    return links
+
+
+@pytest.mark.parametrize("metric", [1, 2])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_build_single_layer_equals_brute_force(metric, seed):
+    """One layer, efConstruction >= N (the insertion beam reaches every node
+    connected to the entry), small caps so that reverse links overflow and
+    are re-selected: the construction equals the brute-force insertion."""
+    r = rng(100 + seed)
+    base = r.integers(0, 10, size=(90, 3)).astype(np.float32)
+    lv = np.zeros(len(base), np.int32)
+    g = oracle.hnsw_build(base, metric, M=3, ef_construction=200, levels=lv, M0=4)
+    want = _brute_build(base, lv, 3, 4, metric, reach_from_entry=True)
+    got = _lists(g, 0)
+    assert got == {v: want[v][0] for v in range(len(base))}
+
+
+@pytest.mark.parametrize("metric", [1, 2])
+def test_build_levels_equals_brute_force(metric):
+    """Several levels, caps above N (no overflow, so every level stays
+    connected and the beam reaches every earlier node on it): each node's
+    lists on every level equal the heuristic over all earlier nodes there."""
+    r = rng(200 + metric)
+    n = 70
+    base = r.integers(0, 12, size=(n, 4)).astype(np.float32)
+    lv = I.hnsw_levels(n, 3, 11 + metric)
+    assert lv.max() >= 2
+    g = oracle.hnsw_build(base, metric, M=n, ef_construction=200, levels=lv, M0=n)
+    want = _brute_build(base, lv, n, n, metric, reach_from_entry=False)
+    for l in range(g["num_levels"]):
+        got = _lists(g, l)
+        assert got == {v: want[v][l] for v in range(n) if lv[v] >= l}, f"level {l}"
