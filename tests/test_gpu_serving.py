@@ -25,16 +25,18 @@ def served():
     idx.close()
 
 
-def _alone(idx, q, p, k, ef):
+def _alone(idx, q, p, k, ef, width=1):
     ids, dist, _ = idx.search(torch.from_numpy(q[None]).cuda(), torch.from_numpy(p[None]).cuda(),
-                              k=int(k), ef=int(ef), k_max=10)
+                              k=int(k), ef=int(ef), k_max=10, width=width)
     return ids.cpu().numpy()[0], dist.cpu().numpy()[0]
 
 
-def test_results_equal_alone_and_in_the_mix(served):
+@pytest.mark.parametrize("width", [1, 3])
+def test_results_equal_alone_and_in_the_mix(served, width):
     U, idx, qs, p, k, ef = served
     arrivals = np.cumsum(np.random.default_rng(3).exponential(10.0, size=len(qs)))  # ~100k QPS
-    srv = U.Server(idx, max_batch=32, streams=4, k_max=10, ef_max=64, max_delay_us=50)
+    srv = U.Server(idx, max_batch=32, streams=4, k_max=10, ef_max=64, max_delay_us=50,
+                   width=width)
     ids, dist, lat = srv.replay(qs, p, k, ef, arrivals)
     st = srv.stats()
     srv.close()
@@ -42,7 +44,7 @@ def test_results_equal_alone_and_in_the_mix(served):
     assert st["batches"] > 1 and st["peak_inflight"] > 1
     assert (lat > 0).all() and st["p99_us"] >= st["p50_us"] > 0
     for i in range(len(qs)):
-        a_ids, a_d = _alone(idx, qs[i], p[i], k[i], ef[i])
+        a_ids, a_d = _alone(idx, qs[i], p[i], k[i], ef[i], width)
         np.testing.assert_array_equal(ids[i], a_ids, err_msg=f"request {i}")
         np.testing.assert_array_equal(dist[i], a_d, err_msg=f"request {i}")
     assert idx.device_status() == 0
