@@ -171,7 +171,7 @@ typedef struct {
 /* CSR form of one HNSW graph, the layout the library's loader also takes:
  * level l holds count[l] nodes (sorted global ids; level 0 may pass NULL
  * for "all nodes, identity"), offsets[count[l]+1] and global-id nbrs. */
-typedef struct {
+typedef struct oracle_csr {
   int32_t num_levels;
   int32_t entry_point;
   int32_t max_degree0;
