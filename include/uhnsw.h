@@ -132,7 +132,12 @@ typedef struct {
                             a negative value stops after the first batch */
   float cutoff;          /* routing: p <= cutoff searches the first graph (G1); 0 => 1.4 */
   int32_t verify_mode;   /* uhnsw_verify_mode */
-  int32_t search_width;  /* beam entries expanded per step; <= 1 => exactly HNSW's order */
+  int32_t search_width;  /* beam entries expanded per step, 0..8; <= 1 => exactly HNSW's
+                            order (the deterministic mode).  w > 1 (the fast mode): each
+                            step takes the first w unexpanded entries of the beam as
+                            parents, gathers their unvisited neighbours in parent order
+                            and keeps the ef nearest of the beam and the new entries; the
+                            results differ from HNSW's order and are judged by recall */
   int32_t persistent;    /* 1: persistent launch pulling queries from a device queue.  The
                             queue is ordered by graph and p form, so that the queries in
                             flight on an SM run the same code.  With per-query ef it is
