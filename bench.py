@@ -47,6 +47,17 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def init_dist(world: int):
+    """One process group for the replicas: host values (timings, the chosen
+    operating point) travel over gloo, CUDA tensors (none on the data path)
+    over NCCL."""
+    if world <= 1:
+        return
+    import torch
+    import torch.distributed as dist
+    dist.init_process_group("cpu:gloo,cuda:nccl" if torch.cuda.is_available() else "gloo")
+
+
 def reduce_max(x: float, world: int) -> float:
     """Max over ranks (host value); identity for one process."""
     if world <= 1:
@@ -58,10 +69,23 @@ def reduce_max(x: float, world: int) -> float:
     return float(t.item())
 
 
+def broadcast_ints(vals, world: int) -> list:
+    """Rank 0's integers on every rank (host values); identity for one process."""
+    if world <= 1:
+        return [int(v) for v in vals]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([int(v) for v in vals], dtype=torch.int64)
+    dist.broadcast(t, src=0)
+    return [int(v) for v in t.tolist()]
+
+
 def barrier(world: int):
+    """Every rank waits for the others (a host all-reduce over gloo)."""
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.barrier()
+        dist.all_reduce(torch.zeros(1, dtype=torch.float64))
 
 
 def aggregate_value(units_per_rank: int, world: int, seconds_max: float) -> float:
@@ -209,10 +233,8 @@ def run_ours(args, log):
     from paper_2605_02030_gb300 import uhnsw as U
 
     rank, local_rank, world = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local_rank)
+    init_dist(world)
     pkg.build()
     w = workload(args)
     t0 = time.time()
@@ -294,7 +316,10 @@ def run_ours(args, log):
         fastest = min(c["ms"] or 0.0 for c in ok)
         best = min((c for c in ok if (c["ms"] or 0.0) <= fastest * 1.01),
                    key=lambda c: c["width"])
-        f["width"], f["ef"] = best["width"], best["ef"]
+        # replicas run rank 0's operating point
+        width, ef = broadcast_ints([best["width"], best["ef"]], world)
+        best = next((c for c in f["calibration"] if c["width"] == width), best)
+        f["width"], f["ef"] = width, ef
         f["recall"], f["recall_min_bin"] = best["recall_at_10"], best["recall_at_10_min_p_bin"]
         f["opts"] = dict(f["opts"], width=f["width"])
 

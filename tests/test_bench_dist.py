@@ -26,11 +26,13 @@ def _worker(rank, world, port, out):
 
     import bench
 
-    dist.init_process_group("gloo", rank=rank, world_size=world)
+    bench.init_dist(world)                     # gloo here: no CUDA device
+    assert dist.get_world_size() == world and dist.get_rank() == rank
     assert bench.dist_env() == (rank, rank, world)
     slow = bench.reduce_max(1.0 + rank, world)       # rank 1 is the slow one
     bench.barrier(world)
-    out[rank] = (slow, bench.aggregate_value(10_000, world, slow))
+    choice = bench.broadcast_ints([2 + rank, 48 - rank], world)   # rank 0's operating point
+    out[rank] = (slow, bench.aggregate_value(10_000, world, slow), tuple(choice))
     dist.destroy_process_group()
 
 
@@ -45,11 +47,12 @@ def test_two_rank_max_and_aggregate():
     for p in procs:
         p.join(120)
         assert p.exitcode == 0
-    assert out[0] == out[1] == (2.0, 10_000.0)
+    assert out[0] == out[1] == (2.0, 10_000.0, (2, 48))
 
 
 def test_single_process_helpers():
     import bench
 
     assert bench.reduce_max(3.5, 1) == 3.5
+    assert bench.broadcast_ints([3, 40], 1) == [3, 40]
     assert bench.aggregate_value(500, 1, 0.25) == 2000.0
