@@ -125,7 +125,7 @@ def test_builder_lp_single_thread_equals_oracle(lib):
     """A graph under a general L_p (p = 0.8, metric 5) on 0/1 data, where every
     |d_j|^0.8 is exactly 0 or 1: one-thread insertion reproduces the oracle's
     FP64 construction under the same p exactly; p = 1 through the same entry
-    point is the L1 graph."""
+    point is the L1 graph, and p = 1.5 the L1.5 graph (metric 4)."""
     r = np.random.default_rng(31)
     base = r.integers(0, 2, size=(1500, 32)).astype(np.float32)
     lv = I.hnsw_levels(len(base), 8, 5)
@@ -134,6 +134,9 @@ def test_builder_lp_single_thread_equals_oracle(lib):
     assert _same_graph(go, gp)
     g1 = U.build_graph(base, U.BASE_LP, 8, 30, lv, threads=1, p=1.0)
     assert _same_graph(oracle.hnsw_build(base, 1, 8, 30, lv), g1)
+    g15 = U.build_graph(base, U.BASE_LP, 8, 30, lv, threads=1, p=1.5)
+    assert _same_graph(oracle.hnsw_build(base, 4, 8, 30, lv), g15)
+    assert _same_graph(U.build_graph(base, U.BASE_L15, 8, 30, lv, threads=1), g15)
 
 
 def test_lp_validation(lib):
