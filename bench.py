@@ -93,6 +93,16 @@ def aggregate_value(units_per_rank: int, world: int, seconds_max: float) -> floa
     return units_per_rank * world / seconds_max
 
 
+def choose_operating_point(calibration, target: float) -> dict:
+    """Among the calibrated (width, ef) pairs whose worst p-bin recall meets
+    the target (all of them if none does), the fastest; a smaller width
+    within 1 % of it is preferred, so that box-to-box noise does not flip the
+    choice.  Pairs without a timing count as equally fast."""
+    ok = [c for c in calibration if c["recall_at_10_min_p_bin"] >= target] or list(calibration)
+    fastest = min(c["ms"] or 0.0 for c in ok)
+    return min((c for c in ok if (c["ms"] or 0.0) <= fastest * 1.01), key=lambda c: c["width"])
+
+
 # ---------------------------------------------------------------- inputs, graphs, ground truth
 def _key(*parts) -> str:
     return hashlib.sha1(repr(parts).encode()).hexdigest()[:16]
@@ -309,13 +319,7 @@ def run_ours(args, log):
                                      "ms": None if ms is None else round(ms, 4)})
             log(f"{name}: width={width} ef={ef} recall={r:.4f} min-bin={rmin:.4f}"
                 + ("" if ms is None else f" {ms:.4f} ms"))
-        ok = [c for c in f["calibration"] if c["recall_at_10_min_p_bin"] >= RECALL_TARGET]
-        ok = ok or f["calibration"]
-        # the fastest; a smaller width within 1 % of it is preferred (stable
-        # choice across boxes)
-        fastest = min(c["ms"] or 0.0 for c in ok)
-        best = min((c for c in ok if (c["ms"] or 0.0) <= fastest * 1.01),
-                   key=lambda c: c["width"])
+        best = choose_operating_point(f["calibration"], RECALL_TARGET)
         # replicas run rank 0's operating point
         width, ef = broadcast_ints([best["width"], best["ef"]], world)
         best = next((c for c in f["calibration"] if c["width"] == width), best)

@@ -1,6 +1,7 @@
-"""bench.py's multi-rank helpers on CPU: two gloo ranks agree on the slowest
-rank's time, and the whole-job value counts every rank's queries (replicas,
-weak scaling, no collective on the data path)."""
+"""bench.py's host logic on CPU: two gloo ranks agree on the slowest rank's
+time and on rank 0's operating point, the whole-job value counts every
+rank's queries (replicas, weak scaling, no collective on the data path), and
+the operating-point choice follows its rule."""
 import os
 import socket
 
@@ -56,3 +57,20 @@ def test_single_process_helpers():
     assert bench.reduce_max(3.5, 1) == 3.5
     assert bench.broadcast_ints([3, 40], 1) == [3, 40]
     assert bench.aggregate_value(500, 1, 0.25) == 2000.0
+
+
+def test_operating_point_choice():
+    import bench
+
+    def c(width, ef, rmin, ms):
+        return {"width": width, "ef": ef, "recall_at_10_min_p_bin": rmin, "ms": ms}
+
+    cal = [c(1, 48, 0.952, 1.85), c(2, 48, 0.953, 1.596), c(3, 48, 0.951, 1.585)]
+    assert bench.choose_operating_point(cal, 0.95)["width"] == 2      # 3 is within 1 %
+    cal[2]["ms"] = 1.40
+    assert bench.choose_operating_point(cal, 0.95)["width"] == 3      # clearly faster
+    cal[2]["recall_at_10_min_p_bin"] = 0.94
+    assert bench.choose_operating_point(cal, 0.95)["width"] == 2      # misses the target
+    low = [c(1, 512, 0.61, 9.0), c(2, 512, 0.62, 8.0)]
+    assert bench.choose_operating_point(low, 0.95)["width"] == 2      # none meets it
+    assert bench.choose_operating_point([c(1, 48, 0.97, None)], 0.95)["ef"] == 48
