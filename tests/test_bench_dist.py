@@ -74,3 +74,22 @@ def test_operating_point_choice():
     low = [c(1, 512, 0.61, 9.0), c(2, 512, 0.62, 8.0)]
     assert bench.choose_operating_point(low, 0.95)["width"] == 2      # none meets it
     assert bench.choose_operating_point([c(1, 48, 0.97, None)], 0.95)["ef"] == 48
+
+
+def test_recall_per_bin_on_the_p_grid():
+    """Every grid value 0.5, 0.6, ..., 2.0 (as FP32) lands in its own bin, and
+    a bin's recall is the mean of its queries' |found & true| / k."""
+    import numpy as np
+
+    import bench
+
+    p = np.repeat(np.array([0.5 + 0.1 * i for i in range(16)], np.float32), 2)
+    gt = np.tile(np.arange(10), (len(p), 1))
+    ids = gt.copy()
+    ids[0, :3] = [-1, 97, 98]          # query 0 (p = 0.5) finds 7 of 10
+    ids[31, 9] = 99                    # query 31 (p = 2.0) finds 9 of 10
+    overall, per = bench.recall_per_bin(ids, gt, p, 10)
+    assert sorted(per) == list(range(16))
+    assert per[0] == (0.7 + 1.0) / 2 and per[15] == (1.0 + 0.9) / 2
+    assert all(per[b] == 1.0 for b in range(1, 15))
+    assert abs(overall - (32 - 0.3 - 0.1) / 32) < 1e-12
