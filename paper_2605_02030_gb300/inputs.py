@@ -13,6 +13,8 @@ Streams for a workload with seed ``s``:
   s+3   HNSW levels of the L1 graph (G1)
   s+4   HNSW levels of the L2 graph (G2)
   s+5   HNSW levels of the L0.5 graph (G0.5, U-HNSW-E)
+  s+6   held-out calibration query vectors (drawn like the queries)
+  s+7   held-out calibration p, k and ef (drawn like the query parameters)
 
 The HNSW level of each node is a random draw of the index construction
 (level = floor(-ln(U) * mL), mL = 1/ln(M), U uniform in (0, 1]); it is drawn
@@ -36,7 +38,7 @@ dataset item is reproduced):
                {32, 64, 128, 256, 512} with ef >= k; BF16 traversal copy.
   unit10m      N=10,000,000 d=96 N(0, I) rows scaled to unit L2 norm, FP16;
                p ~ U(0.5, 2]; k in {10, 50}.
-  sift1m_e     sift1m's base and queries for U-HNSW-E (Section 4.6): graphs
+  sift1m_e     sift1m's base and queries for U-HNSW-E (Section 4.5): graphs
                under L0.5 and L1, cutoff 0.6, p ~ U(0.2, 0.7] (the shifted
                range of the paper's comparison); FP16 traversal copy.
 """
@@ -167,9 +169,10 @@ def query_vectors(w: Workload) -> np.ndarray:
     return _draw_points(w, _rng(w.seed + 1), w.nq, centres)
 
 
-def query_params(w: Workload):
-    """Per-query (p float32 [nq], k int32 [nq], ef int32 [nq])."""
-    rng = _rng(w.seed + 2)
+def query_params(w: Workload, stream: int = 2):
+    """Per-query (p float32 [nq], k int32 [nq], ef int32 [nq]) from stream
+    seed + `stream` (2: the queries; 7: the held-out calibration set)."""
+    rng = _rng(w.seed + stream)
     if w.p_mode == "grid":
         p = P_GRID[rng.integers(0, len(P_GRID), size=w.nq)]
     else:
@@ -185,6 +188,36 @@ def query_params(w: Workload):
     else:
         ef = np.full(w.nq, w.ef, dtype=np.int32)
     return p.astype(np.float32), k, ef
+
+
+def calibration_set(w: Workload):
+    """A held-out query set of the same recipe and size as the workload's
+    queries, from streams of its own: (vectors float32 [nq, d], p, k, ef).
+    A search's beam can be chosen on it and its recall then reported on the
+    workload's own queries."""
+    centres = None if w.kind == "unit" else _centres(w)
+    q = _draw_points(w, _rng(w.seed + 6), w.nq, centres)
+    p, k, ef = query_params(w, stream=7)
+    return q, p, k, ef
+
+
+def p_bin_edges(w: Workload, nbins: int = 16) -> np.ndarray:
+    """Upper edges of `nbins` equal p bins on (p_lo, p_hi] (uniform p), or the
+    grid values themselves (grid p)."""
+    if w.p_mode == "grid":
+        return P_GRID.copy()
+    return (w.p_lo + (w.p_hi - w.p_lo) * np.arange(1, nbins + 1) / nbins).astype(np.float64)
+
+
+def p_bin_of(w: Workload, p: np.ndarray, nbins: int = 16) -> np.ndarray:
+    """Bin index of each p: on the grid, the grid value's position; for
+    uniform p on (lo, hi], bin b holds (lo + b h, lo + (b + 1) h], h = (hi -
+    lo) / nbins."""
+    p = np.asarray(p, np.float64)
+    if w.p_mode == "grid":
+        return np.clip(np.rint((p - float(P_GRID[0])) / 0.1).astype(int), 0, len(P_GRID) - 1)
+    h = (w.p_hi - w.p_lo) / nbins
+    return np.clip(np.ceil((p - w.p_lo) / h - 1e-9).astype(int) - 1, 0, nbins - 1)
 
 
 def hnsw_levels(n: int, M: int, seed: int) -> np.ndarray:
