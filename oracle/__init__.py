@@ -111,6 +111,11 @@ def _load():
                                          P, C.c_int32, P, C.c_float, C.c_int32, C.c_int32,
                                          C.c_int32, C.c_float, C.c_int32, C.c_float, C.c_int32,
                                          C.c_int32, P, P, P]
+    lib.oracle_uhnsw_query_trav.restype = C.c_int
+    lib.oracle_uhnsw_query_trav.argtypes = [C.POINTER(_CSR), C.POINTER(_CSR), C.c_double,
+                                            C.c_double, P, P, C.c_int32, P, C.c_float, C.c_int32,
+                                            C.c_int32, C.c_int32, C.c_float, C.c_int32, C.c_float,
+                                            C.c_int32, C.c_int32, C.c_double, P, P, P, P]
     lib.oracle_uhnsw_query_p.restype = C.c_int
     lib.oracle_uhnsw_query_p.argtypes = [C.POINTER(_CSR), C.POINTER(_CSR), C.c_double, C.c_double,
                                          P, C.c_int32, P, C.c_float, C.c_int32, C.c_int32,
@@ -138,7 +143,7 @@ def lp_sum(x, q, p: float) -> float:
 # Base metrics of the graphs (metric codes): 1 = L1, sum |d_j|; 2 = squared
 # L2, sum d_j^2; 3 = L0.5 without its root, sum |d_j|^(1/2); 4 = L1.5 without
 # its root, sum |d_j|^(3/2).  METRIC_P is the p of each.  U-HNSW uses G1 (L1) and G2 (L2) with cutoff 1.4; U-HNSW-E
-# (Section 4.6) uses G0.5 (L0.5) and G1 (L1) with cutoff 0.6.
+# (Section 4.5) uses G0.5 (L0.5) and G1 (L1) with cutoff 0.6.
 METRIC_P = {1: 1.0, 2: 2.0, 3: 0.5, 4: 1.5}
 
 
@@ -346,6 +351,39 @@ def uhnsw_query(g1, g2, base, q, p: float, k: int, ef: int, t: int = 0, tau: flo
     if rc != 0:
         raise ValueError(f"oracle_uhnsw_query: {rc}")
     return ids, dist, st
+
+
+def uhnsw_query_trav(g1, g2, base, trav, q, p: float, k: int, ef: int, t: int = 0,
+                     tau: float = 0.92, kappa: int = 0, cutoff: float = 1.4, mode: int = 0,
+                     metrics=(1, 2), width: int = 1, tie_tol: float = 0.0, _holders=None):
+    """One query of Algorithm 1 in the precision form: the graph search
+    computes base distances (FP64) on `trav`, rows of the same shape as
+    `base` (the FP16 / BF16 copy's values as FP32), verification and the
+    returned distances use `base`.  A direct query (p = 1 or 2) ranks its
+    whole beam by the exact base distance on `base`.  Returns (ids [k], dist
+    [k], C [t' or ef'] (the candidate list, -1 padded), stats [N_b, N_p,
+    terms, near-tie comparisons of the search at relative tolerance
+    tie_tol])."""
+    base, trav, q = _f32(base), _f32(trav), _f32(q)
+    if trav.shape != base.shape:
+        raise ValueError("trav must have the shape of base")
+    h1 = _holders[0] if _holders else _CSRHolder(g1)
+    h2 = _holders[1] if _holders else _CSRHolder(g2)
+    bpa, bpb = METRIC_P[int(metrics[0])], METRIC_P[int(metrics[1])]
+    tt = max(t if t > 0 else ef, k)
+    cap = max(ef, tt)
+    ids = np.empty(k, np.int64)
+    dist = np.empty(k, np.float64)
+    cand = np.full(cap, -1, np.int64)
+    st = np.zeros(4, np.int64)
+    rc = _load().oracle_uhnsw_query_trav(C.byref(h1.s), C.byref(h2.s), bpa, bpb, _ptr(base),
+                                         _ptr(trav), base.shape[1], _ptr(q), float(p), k, ef, t,
+                                         float(tau), kappa, float(cutoff), mode, int(width),
+                                         float(tie_tol), _ptr(ids), _ptr(dist), _ptr(cand),
+                                         _ptr(st))
+    if rc != 0:
+        raise ValueError(f"oracle_uhnsw_query_trav: {rc}")
+    return ids, dist, cand, st
 
 
 def uhnsw_batch(g1, g2, base, queries, p, k, ef, t=0, tau=0.92, kappa=0, cutoff=1.4, mode=0,

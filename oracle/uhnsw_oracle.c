@@ -39,10 +39,14 @@
  *                         routing (Section 3.1) and the direct K-NN for
  *                         p in {1, 2} (Section 3 introduction); with graphs
  *                         under L0.5 and L1 and cutoff 0.6 it is U-HNSW-E
- *                         (Section 4.6), whose direct K-NN is for p in
+ *                         (Section 4.5), whose direct K-NN is for p in
  *                         {0.5, 1}; oracle_uhnsw_query_p takes the two
  *                         graphs' p instead of metric codes, and
  *                         oracle_uhnsw_query_w a search width as well
+ *   oracle_uhnsw_query_trav  the same with the search on a rounded copy
+ *                         of the rows (the FP16 / BF16 precision form) and
+ *                         verification on the FP32 rows, counting the
+ *                         search's near-tie comparisons
  *
  * Order used everywhere: lexicographic (distance, id), ids ascending on ties.
  * Base metrics (metric codes): 1 = L1, sum |d_j|; 2 = the squared L2 sum
@@ -111,8 +115,23 @@ static double base_root(double s, double bp) {
   return bp == 1.0 ? s : bp == 2.0 ? sqrt(s) : bp == 0.5 ? s * s : pow(s, 1.0 / bp);
 }
 
+/* Near-tie accounting of oracle_uhnsw_query_trav: while g_near is set, every
+ * comparison of two different nodes' finite distances whose gap is at most
+ * g_tie_tol times the larger one (equal values included) is counted.  (A
+ * node compared with itself, as when the popped candidate is W's furthest
+ * entry, decides nothing that a perturbation could change.)  A search that made no such
+ * comparison takes the same decisions under any perturbation of its
+ * distances smaller than half that tolerance.  Thread-local, so that the
+ * queries of the thread driver count independently; NULL everywhere else. */
+static __thread int64_t* g_near = NULL;
+static __thread double g_tie_tol = 0.0;
+
 /* (da, ia) precedes (db, ib) in the (distance, id) order */
 static int pair_less(double da, int64_t ia, double db, int64_t ib) {
+  if (g_near && ia != ib && isfinite(da) && isfinite(db)) {
+    const double m = fabs(da) > fabs(db) ? fabs(da) : fabs(db);
+    if (fabs(da - db) <= g_tie_tol * m) (*g_near)++;
+  }
   if (da < db) return 1;
   if (da > db) return 0;
   return ia < ib;
@@ -722,16 +741,16 @@ int oracle_verify_exact(const float* base, int32_t d, const float* q, double p, 
 }
 
 /*
- * Paper mode (Algorithm 1, lines 6-10):
- *   R <- first K points of C
- *   for each following batch R' of kappa points of C:
- *     R_new <- top-K by L_p of R u R'
- *     if |R_new n R| / K >= tau: return R_new
- *     R <- R_new
- *   return R            (the loop ran out without the test passing)
- * The stop test is evaluated in IEEE single precision, (float)|R_new n R| /
- * (float)K >= tau.  n_lp counts candidates whose L_p sum was computed;
- * n_batches counts batches examined.
+ * Paper mode: the early-terminated verification of Algorithm 1 (Section 3.1).
+ * The current answer starts as the K best (by (S, id)) of the first K valid
+ * candidates of C.  The rest of C is then taken in consecutive batches of
+ * kappa valid candidates (the last batch may be shorter); after each batch
+ * the answer becomes the K best of itself and the batch, and the search
+ * stops as soon as the fraction of the new answer that was already in the
+ * previous one reaches tau.  If C runs out first, the last answer is
+ * returned.  The fraction is compared in IEEE single precision,
+ * (float)overlap / (float)K >= tau.  n_lp counts candidates whose L_p sum was
+ * computed; n_batches counts batches examined.
  */
 int oracle_verify_paper(const float* base, int32_t d, const float* q, double p, const int32_t* cand,
                         int32_t t, int32_t k, int32_t kappa, float tau, int64_t* out_ids,
@@ -799,15 +818,28 @@ int oracle_verify_paper(const float* base, int32_t d, const float* q, double p, 
  * returned distance is S^(1/p).  Counters: stats[0] = base-distance
  * evaluations (N_b), stats[1] = L_p candidates computed (N_p), stats[2] = L_p
  * terms.
+ *
+ * With `trav` given (rows of the same shape as `base`), the graph search
+ * computes its base distances on `trav` (the precision form: a rounded copy
+ * of the rows, here as FP32 values) and verification stays on `base`.  A
+ * direct query (p == the graph's base p) then ranks its whole beam of ef'
+ * by the exact base distance on `base`, so that its returned distances are
+ * those of the FP32 rows.  With tie_tol > 0, stats[3] counts the near-tie
+ * comparisons of the search (see pair_less); cand_out, if given, receives C
+ * (the first t' beam entries, or the whole beam of a direct query on `trav`),
+ * -1 padded.
  */
-int oracle_uhnsw_query_w(const oracle_csr* ga, const oracle_csr* gb, double bpa, double bpb,
-                         const float* base, int32_t d, const float* q, float p, int32_t k,
-                         int32_t ef, int32_t t, float tau, int32_t kappa, float cutoff,
-                         int32_t mode, int32_t width, int64_t* out_ids, double* out_dist,
-                         int64_t* stats) {
+static int uhnsw_query_impl(const oracle_csr* ga, const oracle_csr* gb, double bpa, double bpb,
+                            const float* base, const float* trav, int32_t d, const float* q,
+                            float p, int32_t k, int32_t ef, int32_t t, float tau, int32_t kappa,
+                            float cutoff, int32_t mode, int32_t width, double tie_tol,
+                            int64_t* out_ids, double* out_dist, int64_t* cand_out,
+                            int64_t* stats) {
   if (k < 1 || ef < 1 || width < 1 || !(p > 0.0f) || !(p <= 2.0f)) return OR_EINVAL;
   if (!valid_bp(bpa) || !valid_bp(bpb)) return OR_EINVAL;
-  int64_t nb = 0, np = 0, nterm = 0;
+  const int reduced = trav != NULL;
+  if (!reduced) trav = base;
+  int64_t nb = 0, np = 0, nterm = 0, near = 0;
   const float pa = (float)bpa, pb = (float)bpb;
   int use_a = (p == pa) ? 1 : (p == pb) ? 0 : (p <= cutoff);
   double bp = use_a ? bpa : bpb;
@@ -816,26 +848,31 @@ int oracle_uhnsw_query_w(const oracle_csr* ga, const oracle_csr* gb, double bpa,
   int32_t tt = direct ? k : (t > 0 ? t : ef);
   if (tt < k) tt = k;
   int32_t efp = ef > tt ? ef : tt;
-  int64_t* C = (int64_t*)malloc(sizeof(int64_t) * tt);
-  double* Cd = (double*)malloc(sizeof(double) * tt);
-  int32_t* C32 = (int32_t*)malloc(sizeof(int32_t) * tt);
+  /* a direct query on the rounded copy keeps its whole beam for the re-rank */
+  const int32_t nc = (direct && reduced) ? efp : tt;
+  int64_t* C = (int64_t*)malloc(sizeof(int64_t) * nc);
+  double* Cd = (double*)malloc(sizeof(double) * nc);
+  int32_t* C32 = (int32_t*)malloc(sizeof(int32_t) * nc);
   double* S = (double*)malloc(sizeof(double) * k);
   if (!C || !Cd || !C32 || !S) { free(C); free(Cd); free(C32); free(S); return OR_ENOMEM; }
-  int rc = width == 1 ? oracle_hnsw_search_p(g, base, d, bp, q, efp, tt, C, Cd, &nb)
-                      : oracle_hnsw_search_w(g, base, d, bp, q, efp, tt, width, C, Cd, &nb);
+  if (tie_tol > 0.0) { g_near = &near; g_tie_tol = tie_tol; }
+  int rc = width == 1 ? oracle_hnsw_search_p(g, trav, d, bp, q, efp, nc, C, Cd, &nb)
+                      : oracle_hnsw_search_w(g, trav, d, bp, q, efp, nc, width, C, Cd, &nb);
+  g_near = NULL;
   if (rc != OR_OK) { free(C); free(Cd); free(C32); free(S); return rc; }
-  if (direct) {
+  if (cand_out) for (int32_t j = 0; j < nc; ++j) cand_out[j] = C[j];
+  if (direct && !reduced) {
     for (int32_t j = 0; j < k; ++j) {
       out_ids[j] = C[j];
       out_dist[j] = C[j] < 0 ? INFINITY : base_root(Cd[j], bp);
     }
   } else {
-    for (int32_t j = 0; j < tt; ++j) C32[j] = (int32_t)C[j];
-    if (mode == 0) {
-      oracle_verify_exact(base, d, q, (double)p, C32, tt, k, 1, out_ids, S, &nterm);
-      for (int32_t j = 0; j < tt; ++j) if (C32[j] >= 0) np++;
+    for (int32_t j = 0; j < nc; ++j) C32[j] = (int32_t)C[j];
+    if (mode == 0 || direct) {
+      oracle_verify_exact(base, d, q, (double)p, C32, nc, k, 1, out_ids, S, &nterm);
+      for (int32_t j = 0; j < nc; ++j) if (C32[j] >= 0) np++;
     } else {
-      oracle_verify_paper(base, d, q, (double)p, C32, tt, k, kappa > 0 ? kappa : k,
+      oracle_verify_paper(base, d, q, (double)p, C32, nc, k, kappa > 0 ? kappa : k,
                           tau > 0.0f ? tau : 0.92f, out_ids, S, &np, NULL);
       nterm = np * d;
     }
@@ -843,8 +880,32 @@ int oracle_uhnsw_query_w(const oracle_csr* ga, const oracle_csr* gb, double bpa,
       out_dist[j] = out_ids[j] < 0 ? INFINITY : pow(S[j], 1.0 / (double)p);
   }
   if (stats) { stats[0] = nb; stats[1] = np; stats[2] = nterm; }
+  if (stats && tie_tol > 0.0) stats[3] = near;
   free(C); free(Cd); free(C32); free(S);
   return OR_OK;
+}
+
+int oracle_uhnsw_query_w(const oracle_csr* ga, const oracle_csr* gb, double bpa, double bpb,
+                         const float* base, int32_t d, const float* q, float p, int32_t k,
+                         int32_t ef, int32_t t, float tau, int32_t kappa, float cutoff,
+                         int32_t mode, int32_t width, int64_t* out_ids, double* out_dist,
+                         int64_t* stats) {
+  return uhnsw_query_impl(ga, gb, bpa, bpb, base, NULL, d, q, p, k, ef, t, tau, kappa, cutoff,
+                          mode, width, 0.0, out_ids, out_dist, NULL, stats);
+}
+
+/* Algorithm 1 in the precision form: the graph search on the rounded rows
+ * `trav`, verification on `base` (see uhnsw_query_impl); stats has 4 slots,
+ * the last the number of near-tie comparisons of the search at tie_tol. */
+int oracle_uhnsw_query_trav(const oracle_csr* ga, const oracle_csr* gb, double bpa, double bpb,
+                            const float* base, const float* trav, int32_t d, const float* q,
+                            float p, int32_t k, int32_t ef, int32_t t, float tau, int32_t kappa,
+                            float cutoff, int32_t mode, int32_t width, double tie_tol,
+                            int64_t* out_ids, double* out_dist, int64_t* cand_out,
+                            int64_t* stats) {
+  if (!trav || !(tie_tol >= 0.0)) return OR_EINVAL;
+  return uhnsw_query_impl(ga, gb, bpa, bpb, base, trav, d, q, p, k, ef, t, tau, kappa, cutoff,
+                          mode, width, tie_tol, out_ids, out_dist, cand_out, stats);
 }
 
 int oracle_uhnsw_query_p(const oracle_csr* ga, const oracle_csr* gb, double bpa, double bpb,

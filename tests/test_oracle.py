@@ -362,7 +362,7 @@ def test_recall_definition():
     assert oracle.recall([[1, 2], [5, 6]], [[1, 2], [6, 7]]) == pytest.approx(0.75)
 
 
-# ----------------------------------------------------------------- U-HNSW-E (Section 4.6)
+# ----------------------------------------------------------------- U-HNSW-E (Section 4.5)
 def test_base_dist_l05_pins():
     """Metric 3 is sum |d_j|^(1/2): a hand value, and scipy's Minkowski p = 0.5
     distance, which is that sum squared."""
@@ -696,3 +696,117 @@ def test_build_levels_equals_brute_force(metric):
     for l in range(g["num_levels"]):
         got = _lists(g, l)
         assert got == {v: want[v][l] for v in range(n) if lv[v] >= l}, f"level {l}"
+
+
+# ----------------------------------------------------------------- precision form (rounded rows)
+def _f16_rows(x):
+    return x.astype(np.float16).astype(np.float32)
+
+
+def test_trav_equal_to_base_is_the_plain_query(mixture_small):
+    """With the traversal rows equal to the FP32 rows, the precision form is
+    Algorithm 1 itself: same ids and distances for general p, p = 1 and
+    p = 2 (the direct queries' beam re-rank keeps the beam's order), at
+    widths 1 and 2, in both verification modes."""
+    w, base, qs, p, g1, g2 = mixture_small
+    ps = np.concatenate([p[:6], [1.0, 2.0]]).astype(np.float32)
+    for width in (1, 2):
+        for mode in (0, 1):
+            for i, pp in enumerate(ps):
+                a = oracle.uhnsw_query(g1, g2, base, qs[i], float(pp), 10, 40, mode=mode,
+                                       width=width)
+                b = oracle.uhnsw_query_trav(g1, g2, base, base, qs[i], float(pp), 10, 40,
+                                            mode=mode, width=width)
+                np.testing.assert_array_equal(a[0], b[0])
+                np.testing.assert_allclose(a[1], b[1], rtol=1e-12)
+                assert a[2][0] == b[3][0]                 # same N_b
+
+
+def test_trav_full_beam_ranks_by_rounded_rows(mixture_small):
+    """ef >= N on a connected layer 0: the candidate list is the exact top-t
+    under the base metric of the ROUNDED rows (brute force on them), and the
+    answer is the exact L_p top-K over that list on the FP32 rows; a direct
+    p = 1 query returns the FP32 L1 top-K of its whole (rounded-row) beam."""
+    w, base, qs, p, g1, g2 = mixture_small
+    trav = _f16_rows(base)
+    assert (trav != base).mean() > 0.5
+    n, t = len(base), 25
+    for i in range(4):
+        pp = float(p[i])
+        metric, g = ((1, "cityblock") if pp <= 1.4 else (2, "sqeuclidean"))
+        D = cdist(qs[i:i + 1].astype(np.float64), trav.astype(np.float64), g)[0]
+        top_t = np.lexsort((np.arange(n), D))[:t]
+        ids, dist, cand, st = oracle.uhnsw_query_trav(g1, g2, base, trav, qs[i], pp, 10, n, t=t)
+        np.testing.assert_array_equal(cand[:t], top_t)
+        S = (np.abs(base[top_t].astype(np.float64) - qs[i].astype(np.float64)) ** pp).sum(1)
+        order = top_t[np.lexsort((top_t, S))][:10]
+        np.testing.assert_array_equal(ids, order)
+        np.testing.assert_allclose(dist, np.sort(S)[:10] ** (1 / pp), rtol=1e-12)
+    D1 = cdist(qs[:1].astype(np.float64), base.astype(np.float64), "cityblock")[0]
+    ids, dist, cand, st = oracle.uhnsw_query_trav(g1, g2, base, trav, qs[0], 1.0, 10, n)
+    order = np.lexsort((np.arange(n), D1))[:10]
+    np.testing.assert_array_equal(ids, order)
+    np.testing.assert_allclose(dist, D1[order], rtol=1e-12)
+
+
+def test_near_tie_counter_sees_equal_distances():
+    """Two points at the same distance from the query (mirror images) make
+    the search compare equal values: counted at any tolerance; points far
+    apart in distance are not counted at a small tolerance; the count never
+    falls as the tolerance grows."""
+    base = np.array([[0.0], [10.0], [-3.0], [3.0], [7.5], [-8.0]], np.float32)
+    g = oracle.hnsw_build(base, 1, M=4, ef_construction=10, levels=np.zeros(6, np.int32), M0=8)
+    q = np.array([0.0], np.float32)
+    counts = []
+    for tol in (1e-12, 1e-6, 0.3, 1.0):
+        _, _, _, st = oracle.uhnsw_query_trav(g, g, base, base, q, 1.0, 3, 6, tie_tol=tol)
+        counts.append(int(st[3]))
+    assert counts[0] >= 1                      # |-3| == |3|
+    assert counts == sorted(counts)
+    base2 = np.array([[0.0], [10.0], [-3.0], [3.5], [7.5], [-8.0]], np.float32)
+    g2 = oracle.hnsw_build(base2, 1, M=4, ef_construction=10, levels=np.zeros(6, np.int32), M0=8)
+    _, _, _, st = oracle.uhnsw_query_trav(g2, g2, base2, base2, q, 1.0, 3, 6, tie_tol=1e-6)
+    assert st[3] == 0
+
+
+def _round_mantissa(x, keep):
+    """FP32 values rounded (to nearest, ties to even) to `keep` mantissa bits."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    drop = 23 - keep
+    r = ((u + (1 << (drop - 1)) - 1 + ((u >> drop) & 1)) >> drop) << drop
+    return r.astype(np.uint32).view(np.float32)
+
+
+def test_tie_free_searches_survive_perturbation(mixture_small):
+    """The certificate behind the float-data parity rule: if the search on
+    one copy of the rows made no comparison within tol (relative), a second
+    copy whose every base distance differs from the first by less than tol / 2
+    (relative) gives the same candidate list.  The second copies are the FP32
+    rows rounded to 12 and 14 mantissa bits; tol is just over twice their
+    largest relative distance difference from the FP32 rows (brute force
+    over every node).  Every query whose candidate lists differ must have
+    counted a near-tie, some lists do differ, and some searches are
+    tie-free."""
+    w, base, qs, p, g1, g2 = mixture_small
+    nq = 20
+    flagged = diverged = total = 0
+    for keep in (12, 14):
+        trav = _round_mantissa(base, keep)
+        rel = 0.0
+        for name in ("cityblock", "sqeuclidean"):
+            A = cdist(qs[:nq].astype(np.float64), base.astype(np.float64), name)
+            B = cdist(qs[:nq].astype(np.float64), trav.astype(np.float64), name)
+            rel = max(rel, float((np.abs(A - B) / np.maximum(np.maximum(A, B), 1e-300)).max()))
+        tol = 2.0 * rel * 1.01
+        for i in range(nq):
+            for width in (1, 2):
+                a = oracle.uhnsw_query_trav(g1, g2, base, base, qs[i], float(p[i]), 10, 32,
+                                            width=width, tie_tol=tol)
+                b = oracle.uhnsw_query_trav(g1, g2, base, trav, qs[i], float(p[i]), 10, 32,
+                                            width=width, tie_tol=tol)
+                if a[3][3] == 0:
+                    np.testing.assert_array_equal(a[2], b[2])
+                flagged += int(a[3][3] > 0)
+                diverged += int(not np.array_equal(a[2], b[2]))
+                total += 1
+    assert diverged >= 1 and flagged < total
