@@ -10,7 +10,7 @@
  * L_p ("Candidate verification", Algorithm 1 lines 6-10).  p == 1 and p == 2
  * search G1 / G2 for the K nearest directly, without verification (Section 3,
  * introduction).  In general a query whose p equals a graph's base p is
- * answered directly on that graph; U-HNSW-E (Section 4.6) loads graphs under
+ * answered directly on that graph; U-HNSW-E (Section 4.5) loads graphs under
  * L0.5 and L1 (uhnsw_load_opts.base_metric) and routes with cutoff 0.6.
  *
  * Conventions for every entry point:
@@ -102,7 +102,7 @@ typedef struct {
   uhnsw_dtype traverse_dtype;
   /* base metrics of the two graph slots; 0 => UHNSW_BASE_L1 for the first
    * (g1) and UHNSW_BASE_L2 for the second (g2), which is U-HNSW.  U-HNSW-E
-   * (Section 4.6) loads a graph built under L0.5 as g1 and one built under
+   * (Section 4.5) loads a graph built under L0.5 as g1 and one built under
    * L1 as g2 ({UHNSW_BASE_L05, UHNSW_BASE_L1}) and searches with cutoff 0.6.
    * The first slot's base p must be below the second's. */
   int32_t base_metric[2];
@@ -357,6 +357,32 @@ void uhnsw_free(uhnsw_index* idx);
 const char* uhnsw_last_error(void);
 
 /* ------------------------------------------------------------------------
+ * Measurement probes: the peak rates that roofline fractions are stated
+ * against, measured on the current device (not part of the query path; the
+ * paper has no counterpart).  Each launches once untimed, then once between
+ * two events on `stream`, and synchronises it.  Errors: EINVAL, ECUDA.
+ * ---------------------------------------------------------------------- */
+
+/* SFU rate of the general-p verification term 2^(p log2 |d|): blocks_per_sm
+ * (1..64) blocks of 256 threads per SM, each thread running 8 independent
+ * chains of `iters` links x <- 2^(c log2 x) (lg2.approx, ex2.approx).
+ * *elapsed_ms = the timed launch; *ops = SFU operations it executed
+ * (2 x 8 x iters x threads).  Allocates a small sink buffer. */
+int uhnsw_probe_sfu(int32_t blocks_per_sm, int32_t iters, float* elapsed_ms, double* ops,
+                    void* stream);
+
+/* Random-row gather bandwidth: every warp of blocks_per_sm blocks of 256
+ * threads per SM reads `per_warp` (a positive multiple of 128) rows of
+ * `row_bytes` (a multiple of 16) bytes, chosen by a hash of (warp, i), with
+ * 16-byte loads, four rows per lane group in flight.  buf: device, 16-byte
+ * aligned, rows x row_bytes bytes (rows < 2^32).  A buffer smaller than L2
+ * measures L2 gathers (after the untimed launch has warmed it); a larger one
+ * measures HBM gathers.  *bytes = row bytes read by the timed launch.
+ * Allocates a small sink buffer. */
+int uhnsw_probe_gather(const void* buf, int64_t rows, int32_t row_bytes, int32_t per_warp,
+                       int32_t blocks_per_sm, float* elapsed_ms, double* bytes, void* stream);
+
+/* ------------------------------------------------------------------------
  * Serving: continuous batching over a resident index.  The paper answers one
  * query at a time (Section 4.1.2 measures per-query time); this server lets
  * requests that arrive while others are on the GPU join the next batch.
@@ -379,13 +405,14 @@ typedef struct {
 } uhnsw_server_opts;
 
 typedef struct {
-  int64_t completed;     /* requests finished (latencies recorded) */
+  int64_t completed;     /* requests finished since the server started */
   int64_t batches;       /* launches */
   double mean_batch;     /* queries per launch */
   int64_t peak_inflight; /* most queries admitted and unfinished at once */
   int64_t peak_state;    /* most search-state bytes admitted at once (<= state_budget
                             unless a single request exceeds it) */
-  double mean_us, p50_us, p99_us, max_us; /* submit -> result on the host */
+  double mean_us, p50_us, p99_us, max_us; /* submit -> result on the host, over the last
+                                             2^20 finished requests */
   int32_t error;         /* first failure of a launch (0 if none) */
   int32_t reserved;
 } uhnsw_server_report;
@@ -406,7 +433,8 @@ int uhnsw_server_submit(uhnsw_server* s, const float* q, float p, int32_t k, int
  * finished, else *done = 0. */
 int uhnsw_server_poll(uhnsw_server* s, uint64_t ticket, int64_t* ids, float* dist, int32_t* done);
 
-/* Blocks until the request finishes (or timeout_ms: UHNSW_ETIMEOUT). */
+/* Blocks until the request finishes (or timeout_ms: UHNSW_ETIMEOUT).  A
+ * ticket released meanwhile by another poll / wait gives UHNSW_EINVAL. */
 int uhnsw_server_wait(uhnsw_server* s, uint64_t ticket, int64_t* ids, float* dist,
                       int32_t timeout_ms);
 

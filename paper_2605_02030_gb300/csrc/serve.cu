@@ -85,8 +85,11 @@ struct uhnsw_server {
   bool stop = false;
   int32_t error = 0;
   std::thread dispatcher, completer;
-  // statistics
+  // statistics: latencies of the last kLatWindow requests (a ring), and the
+  // number finished in all
+  static constexpr size_t kLatWindow = size_t(1) << 20;
   std::vector<double> lat_us;
+  int64_t completed = 0;
   int64_t batches = 0, batched_queries = 0, peak_inflight = 0, inflight_queries = 0;
   int64_t peak_state = 0;
 };
@@ -251,7 +254,10 @@ void completer_main(uhnsw_server* s, int device) {
         r.status = q == cudaSuccess ? 0 : UHNSW_ECUDA;
         r.done = true;
         r.t_done = now;
-        s->lat_us.push_back(std::chrono::duration<double, std::micro>(now - r.t_submit).count());
+        const double us = std::chrono::duration<double, std::micro>(now - r.t_submit).count();
+        if (s->lat_us.size() < uhnsw_server::kLatWindow) s->lat_us.push_back(us);
+        else s->lat_us[(size_t)s->completed % uhnsw_server::kLatWindow] = us;
+        ++s->completed;
       }
       if (q != cudaSuccess) s->error = UHNSW_ECUDA;
       L.busy = false;
@@ -382,9 +388,15 @@ extern "C" int uhnsw_server_wait(uhnsw_server* s, uint64_t ticket, int64_t* ids,
   std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->reqs.find(ticket);
   if (it == s->reqs.end()) return fail(UHNSW_EINVAL, "uhnsw_server_wait: unknown ticket");
-  const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms),
-                                      [&] { return s->reqs[ticket].done; });
+  // find(), not operator[]: another caller may release the ticket meanwhile
+  auto finished_or_gone = [&] {
+    auto jt = s->reqs.find(ticket);
+    return jt == s->reqs.end() || jt->second.done;
+  };
+  const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), finished_or_gone);
   if (!ok) return fail(UHNSW_ETIMEOUT, "uhnsw_server_wait: not done after %d ms", timeout_ms);
+  if (s->reqs.find(ticket) == s->reqs.end())
+    return fail(UHNSW_EINVAL, "uhnsw_server_wait: ticket released by another call");
   const int st = take_result(s, ticket, ids, dist, nullptr);
   return st == 0 ? UHNSW_OK : fail(st, "uhnsw_server_wait: request failed (%d)", st);
 }
@@ -412,8 +424,15 @@ extern "C" int uhnsw_server_replay(uhnsw_server* s, const float* q, const float*
   const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms);
   std::unique_lock<std::mutex> lk(s->mu);
   for (int64_t i = 0; i < nq; ++i) {
-    const bool ok = s->cv_done.wait_until(lk, deadline, [&] { return s->reqs[tickets[i]].done; });
+    const uint64_t tk = tickets[i];
+    const bool ok = s->cv_done.wait_until(lk, deadline, [&] {
+      auto jt = s->reqs.find(tk);
+      return jt == s->reqs.end() || jt->second.done;
+    });
     if (!ok) return fail(UHNSW_ETIMEOUT, "uhnsw_server_replay: request %lld not done", (long long)i);
+    if (s->reqs.find(tk) == s->reqs.end())
+      return fail(UHNSW_EINVAL, "uhnsw_server_replay: request %lld released by another call",
+                  (long long)i);
     for (int j = k[i]; j < kmax; ++j) {
       if (out_ids) out_ids[i * kmax + j] = -1;
       if (out_dist) out_dist[i * kmax + j] = __builtin_huge_valf();
@@ -431,7 +450,7 @@ extern "C" int uhnsw_server_stats(uhnsw_server* s, uhnsw_server_report* out) {
   if (!s || !out) return fail(UHNSW_EINVAL, "uhnsw_server_stats: NULL argument");
   std::lock_guard<std::mutex> lk(s->mu);
   std::memset(out, 0, sizeof(*out));
-  out->completed = (int64_t)s->lat_us.size();
+  out->completed = s->completed;
   out->batches = s->batches;
   out->mean_batch = s->batches ? (double)s->batched_queries / (double)s->batches : 0.0;
   out->peak_inflight = s->peak_inflight;

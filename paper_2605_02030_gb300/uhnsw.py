@@ -52,7 +52,7 @@ class _LoadOpts(C.Structure):
 # 4 = L1.5 sum, 5 = the L_p sum of a slot's base_p (any 0 < p <= 2).
 BASE_L1, BASE_L2, BASE_L05, BASE_L15, BASE_LP = 1, 2, 3, 4, 5
 U_HNSW = (BASE_L1, BASE_L2)        # G1 and G2, cutoff 1.4
-U_HNSW_E = (BASE_L05, BASE_L1)     # G0.5 and G1, cutoff 0.6 (Section 4.6)
+U_HNSW_E = (BASE_L05, BASE_L1)     # G0.5 and G1, cutoff 0.6 (Section 4.5)
 
 
 class _SearchOpts(C.Structure):
@@ -83,7 +83,7 @@ EXPORTS = ("uhnsw_load", "uhnsw_search", "uhnsw_search_host", "uhnsw_verify", "u
            "uhnsw_server_destroy", "uhnsw_autotune", "uhnsw_autotune_save", "uhnsw_autotune_load",
            "uhnsw_index_info", "uhnsw_device_status", "uhnsw_free", "uhnsw_last_error",
            "uhnsw_build_graph", "uhnsw_build_graph_gpu", "uhnsw_build_graph_lp",
-           "uhnsw_built_graph", "uhnsw_built_free")
+           "uhnsw_built_graph", "uhnsw_built_free", "uhnsw_probe_sfu", "uhnsw_probe_gather")
 
 
 def library_path() -> str:
@@ -150,6 +150,10 @@ def load_library():
     lib.uhnsw_build_graph_gpu.argtypes = [P, I64, I32, I32, I32, I32, P, P]
     lib.uhnsw_build_graph_lp.restype = C.c_int
     lib.uhnsw_build_graph_lp.argtypes = [P, I64, I32, C.c_float, I32, I32, P, I32, I32, P]
+    lib.uhnsw_probe_sfu.restype = C.c_int
+    lib.uhnsw_probe_sfu.argtypes = [I32, I32, P, P, P]
+    lib.uhnsw_probe_gather.restype = C.c_int
+    lib.uhnsw_probe_gather.argtypes = [P, I64, I32, I32, I32, P, P, P]
     lib.uhnsw_built_graph.restype = C.c_int
     lib.uhnsw_built_graph.argtypes = [P, P]
     lib.uhnsw_built_free.restype = None
@@ -175,6 +179,28 @@ def _stream_ptr(stream) -> C.c_void_p:
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
     return C.c_void_p(s.cuda_stream)
+
+
+# ----------------------------------------------------------------- measurement probes
+def probe_sfu(blocks_per_sm: int = 8, iters: int = 4096, stream=None):
+    """SFU (lg2 + ex2) rate on the current device: (ms, operations) of one
+    timed launch of uhnsw_probe_sfu."""
+    ms, ops = C.c_float(0), C.c_double(0)
+    _check(load_library().uhnsw_probe_sfu(blocks_per_sm, iters, C.byref(ms), C.byref(ops),
+                                          _stream_ptr(stream)))
+    return ms.value, ops.value
+
+
+def probe_gather(buf, row_bytes: int, per_warp: int = 1024, blocks_per_sm: int = 8, stream=None):
+    """Random-row gather rate from the device tensor `buf` (its bytes viewed
+    as rows of row_bytes): (ms, bytes) of one timed launch of
+    uhnsw_probe_gather."""
+    rows = buf.numel() * buf.element_size() // row_bytes
+    ms, nbytes = C.c_float(0), C.c_double(0)
+    _check(load_library().uhnsw_probe_gather(_t_ptr(buf), rows, row_bytes, per_warp,
+                                             blocks_per_sm, C.byref(ms), C.byref(nbytes),
+                                             _stream_ptr(stream)))
+    return ms.value, nbytes.value
 
 
 # ----------------------------------------------------------------- graph building
