@@ -56,7 +56,7 @@ inline v4f load4(const float* p) {
 }
 
 // Base metric in FP32: metric 1 -> sum |d_j|, metric 2 -> sum d_j^2,
-// metric 3 -> sum |d_j|^(1/2) (the L0.5 graph of U-HNSW-E, Section 4.6),
+// metric 3 -> sum |d_j|^(1/2) (the L0.5 graph of U-HNSW-E, Section 4.5),
 // metric 4 -> sum |d_j|^(3/2) (an L1.5 graph, Section 4.3's fixed-p HNSW),
 // metric 5 -> sum |d_j|^bp (the fixed-p HNSW at any other p).
 // Four independent 4-wide partial sums, then a fixed combination order; the

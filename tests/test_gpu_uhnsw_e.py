@@ -1,4 +1,4 @@
-"""U-HNSW-E (Section 4.6) on the GPU: graphs under L0.5 (G0.5) and L1 (G1),
+"""U-HNSW-E (Section 4.5) on the GPU: graphs under L0.5 (G0.5) and L1 (G1),
 cutoff 0.6, p in [0.2, 1].  Parity with the oracle's Algorithm 1 run with the
 same graphs and base metrics.
 
