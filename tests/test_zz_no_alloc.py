@@ -5,9 +5,10 @@ device memory belongs to another framework's caching allocator, and
 latency-critical code that must not hit the device-wide synchronisation of
 cudaMalloc / cudaFree cannot use uhnsw_exact, which grows its workspace on
 demand.  uhnsw_exact_static keeps that workspace in a fixed device array
-instead.  This test calls both entry points through the C ABI and checks that
-the allocation-free one returns the same answer on two calls in a row (the
-array keeps the previous call's contents, which must not leak into the next).
+instead.  This test calls both entry points through the C ABI and checks, on
+two calls in a row, that the allocation-free one returns the oracle's exact
+FP64 answer and the same answer as uhnsw_exact (the array keeps the previous
+call's contents, which must not leak into the next).
 The file is collected last so that a run stopping at the first failure has
 already run every other test.
 """
@@ -15,6 +16,8 @@ import ctypes as C
 
 import numpy as np
 import pytest
+
+import oracle
 
 from helpers import check_topk, oracle_graphs, workload_arrays
 
@@ -54,10 +57,15 @@ def test_exact_static_matches_exact_twice():
         torch.cuda.synchronize()
         a_ids, a_d = ids_a.cpu().numpy(), dist_a.cpu().numpy()
         b_ids, b_d = ids_b.cpu().numpy(), dist_b.cpu().numpy()
+        ref_ids, _ = oracle.exact_knn(base, qs[lo:hi], p[lo:hi], k)
         for i in range(nq):
-            # the same tolerance rule as every parity test: ids equal except
-            # near-ties, distances within 2e-5 of the FP64 oracle
-            check_topk(base, qs[lo + i], p[lo + i], b_ids[i], b_d[i], a_ids[i], k, f"q{lo + i}")
+            # the same tolerance rule as every parity test: ids equal to the
+            # oracle's exact top-k except near-ties, distances within 2e-5 of
+            # the FP64 oracle; and the allocating entry point agrees
+            check_topk(base, qs[lo + i], p[lo + i], b_ids[i], b_d[i], ref_ids[i], k,
+                       f"static q{lo + i}")
+            check_topk(base, qs[lo + i], p[lo + i], b_ids[i], b_d[i], a_ids[i], k,
+                       f"static vs uhnsw_exact q{lo + i}")
         np.testing.assert_allclose(b_d, a_d, rtol=2e-5)
     # a request larger than the fixed array is refused before any work
     big = 32 * 1024 * 1024 // (8 * k) + 1
