@@ -169,6 +169,20 @@ typedef struct {
                                   derives t per p from idealized recall. */
   const float* tau_per_query;  /* device [nq] or NULL: query i's tau in place of tau (0 =>
                                   0.92, negative => stop after the first batch) */
+  int32_t hash_bits;     /* visited table of 1 << hash_bits slots per query; 0 => the
+                            smallest power of two >= 4 (ef' + search_width * M0), at least
+                            2^9.  Allowed: from the smallest power of two >= 2 (ef' +
+                            search_width * M0) up to 2^15 (else UHNSW_EINVAL).  The size
+                            does not change any result (a table past half full is cleared
+                            and refilled with the beam, which cannot change the beam); a
+                            smaller table re-evaluates more nodes, a larger one takes
+                            shared memory from other queries. */
+  int32_t verify_groups; /* verification: 32-dimension groups accumulated between two
+                            tests of a candidate's partial sum against the running k-th
+                            best sum, 1..16; 0 => 1.  Every lane accumulates its elements
+                            in the same order whatever the value, so sums and results do
+                            not depend on it; it trades drop-test work for candidates
+                            summed further before they are dropped. */
 } uhnsw_search_opts;
 
 /*
@@ -319,10 +333,13 @@ int uhnsw_exact_static(uhnsw_index* idx, const float* q, const float* p, int64_t
  * `stream`, and records the fastest for the bucket (traversal dtype, beam
  * next_pow2(max(ef, k)), k next_pow2(k)) in the index; uhnsw_search with
  * opts->query_threads == 0 then uses it.  Candidates: the warp-per-query
- * kernel with each compiled team width that covers a row (8, 16, 32 lanes)
- * and 4, 8 or 16 staged verification rows; the block-per-query kernel.  The
- * candidates run the same algorithm in the same order; their distances can
- * differ only by FP32 summation order.  `base` supplies the other options
+ * kernel with each compiled team width that covers a row (8, 16, 32 lanes),
+ * 4, 8 or 16 staged verification rows, the default visited table or one
+ * twice its size, and a drop test every 1, 2 or 4 verification groups; the
+ * block-per-query kernel.  The candidates run the same algorithm in the same
+ * order; their distances can differ only by the FP32 summation order of the
+ * team width (table size, staging and drop-test interval change no sum).
+ * hash_bits and verify_groups set in `base` are kept, not searched.  `base` supplies the other options
  * (may be NULL); `best` (may be NULL) receives the chosen options and
  * `best_ms` (may be NULL) its median time.  The paper has no counterpart
  * (its queries run one at a time on a CPU).  Synchronises `stream`.
@@ -333,8 +350,9 @@ int uhnsw_autotune(uhnsw_index* idx, const float* q, const float* p, int64_t nq,
                    uhnsw_search_opts* best, float* best_ms);
 
 /* Writes / reads the tuned configurations as text lines
- * "dtype d ef_bucket k_bucket query_threads team_lanes stage_bytes"; load
- * keeps only lines matching this index's dtype and d. */
+ * "dtype d ef_bucket k_bucket query_threads team_lanes stage_bytes hash_bits
+ * verify_groups"; load keeps only lines matching this index's dtype and d
+ * (lines of seven fields, without the last two, load with both 0). */
 int uhnsw_autotune_save(const uhnsw_index* idx, const char* path);
 int uhnsw_autotune_load(uhnsw_index* idx, const char* path);
 

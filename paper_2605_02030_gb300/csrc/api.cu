@@ -386,6 +386,16 @@ struct Prepared {
   std::vector<Launch> launches;
 };
 
+// Visited-table size (log2 slots) of a launch whose beam is at most `bound`:
+// the caller's choice (already checked against its minimum, and kept inside
+// the minimum of this bound's table too), else 4 (bound + width * M0) rounded
+// up to a power of two, at least 2^9.
+int visited_bits(int asked, int bound, int width, int deg0) {
+  const int def = std::max(9, next_pow2_bits(4ll * (bound + width * deg0)));
+  if (asked <= 0) return def;
+  return std::max(asked, next_pow2_bits(2ll * (bound + width * deg0)));
+}
+
 // Validates host-side search arguments and fills the launch description.
 int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32_t* k,
                    const int32_t* ef, int64_t nq, int32_t k_max, int32_t ef_default,
@@ -419,6 +429,10 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
     return fail(UHNSW_EINVAL, "uhnsw_search: team_lanes=%d not 0, 8, 16 or 32", opts.team_lanes);
   if (opts.stage_bytes < 0 || opts.stage_bytes > 64 * 1024)
     return fail(UHNSW_EINVAL, "uhnsw_search: stage_bytes=%d not in [0, 65536]", opts.stage_bytes);
+  if (opts.hash_bits < 0 || opts.hash_bits > 15)
+    return fail(UHNSW_EINVAL, "uhnsw_search: hash_bits=%d not in [0, 15]", opts.hash_bits);
+  if (opts.verify_groups < 0 || opts.verify_groups > 16)
+    return fail(UHNSW_EINVAL, "uhnsw_search: verify_groups=%d not in [0, 16]", opts.verify_groups);
 
   int ef_cap;
   const bool per_query_beam = ef != nullptr || opts.t_per_query != nullptr;
@@ -439,6 +453,8 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
         opts.query_threads = tv.second.query_threads;
         opts.team_lanes = tv.second.team_lanes;
         opts.stage_bytes = tv.second.stage_bytes;
+        if (opts.hash_bits == 0) opts.hash_bits = tv.second.hash_bits;
+        if (opts.verify_groups == 0) opts.verify_groups = tv.second.verify_groups;
         break;
       }
   }
@@ -452,6 +468,9 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   const bool want_warp = opts.query_threads != kBlock;
   if (next_pow2_bits(4ll * (ef_cap + width * deg0)) > 15)
     return fail(UHNSW_ECAPACITY, "uhnsw_search: visited table too large");
+  if (opts.hash_bits != 0 && opts.hash_bits < next_pow2_bits(2ll * (ef_cap + width * deg0)))
+    return fail(UHNSW_EINVAL, "uhnsw_search: hash_bits=%d below the minimum %d for beam %d",
+                opts.hash_bits, next_pow2_bits(2ll * (ef_cap + width * deg0)), ef_cap);
   const int chunks = idx->d_pad / (idx->tdtype == UHNSW_F32 ? 4 : 8);
   TeamShape sh{0, 0};
   WarpShape wsh{0, 0, 0};
@@ -494,6 +513,7 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   a.cutoff = opts.cutoff > 0.f ? opts.cutoff : 1.4f;
   a.mode = opts.verify_mode;
   a.width = width;
+  a.vgroups = opts.verify_groups > 0 ? opts.verify_groups : 1;
   a.vcap = 0;
   a.out_ids = out_ids;
   a.out_dist = out_dist;
@@ -516,7 +536,7 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   auto describe = [&](int bound, Launch* Lo) -> int {
     Lo->a = a;
     Lo->a.ef_cap = bound;
-    Lo->a.hash_bits = std::max(9, next_pow2_bits(4ll * (bound + width * deg0)));
+    Lo->a.hash_bits = visited_bits(opts.hash_bits, bound, width, deg0);
     bool w = want_warp;
     for (int attempt = 0; attempt < 2; ++attempt) {
       const int cmax = std::max({width * deg0, deg, w ? 4 : kBlock / 8});
@@ -751,6 +771,8 @@ extern "C" int uhnsw_verify(uhnsw_index* idx, const float* q, const float* p, co
   if (opts.verify_mode != UHNSW_VERIFY_EXACT && opts.verify_mode != UHNSW_VERIFY_PAPER)
     return fail(UHNSW_EINVAL, "uhnsw_verify: verify_mode");
   if (opts.kappa < 0 || !std::isfinite(opts.tau)) return fail(UHNSW_EINVAL, "uhnsw_verify: kappa/tau");
+  if (opts.verify_groups < 0 || opts.verify_groups > 16)
+    return fail(UHNSW_EINVAL, "uhnsw_verify: verify_groups=%d not in [0, 16]", opts.verify_groups);
   if (nq == 0) return UHNSW_OK;
   QueryArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -765,6 +787,7 @@ extern "C" int uhnsw_verify(uhnsw_index* idx, const float* q, const float* p, co
   a.kappa = opts.kappa;
   a.tau = opts.tau != 0.f ? opts.tau : 0.92f;
   a.mode = opts.verify_mode;
+  a.vgroups = opts.verify_groups > 0 ? opts.verify_groups : 1;
   a.cmax = kBlock / 8;
   a.vcap = std::max(t, 1);
   a.out_ids = out_ids;
@@ -773,8 +796,7 @@ extern "C" int uhnsw_verify(uhnsw_index* idx, const float* q, const float* p, co
   a.err = idx->err;
   a.cand = cand;
   a.cand_t = t;
-  const SmemLayout L(idx->d_pad, 0, 0, a.cmax, k, a.vcap);
-  cudaError_t e = launch_verify(a, kBlock, L.total, (cudaStream_t)stream);
+  cudaError_t e = launch_wverify(a, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "uhnsw_verify: launch");
   return UHNSW_OK;
 }
@@ -955,7 +977,7 @@ int64_t uhnsw_internal::query_state_bytes(const uhnsw_index* idx, int32_t ef, in
     }
   const int efp = std::max(ef, k);
   const int cmax = std::max({width * deg0, deg, warp ? 4 : kBlock / 8});
-  const int hb = std::max(9, next_pow2_bits(4ll * (efp + width * deg0)));
+  const int hb = visited_bits(opts.hash_bits, efp, width, deg0);
   int stage = 0;
   if (warp) {
     const int vrow = idx->d_pad * 4;
@@ -979,24 +1001,45 @@ extern "C" int uhnsw_autotune(uhnsw_index* idx, const float* q, const float* p, 
   if (efp > UHNSW_MAX_EF) return fail(UHNSW_EINVAL, "uhnsw_autotune: beam %d", efp);
   const int chunks = idx->d_pad / (idx->tdtype == UHNSW_F32 ? 4 : 8);
   std::vector<uhnsw_search_opts> cands;
+  int deg0 = 0;
+  for (auto& G : idx->g)
+    if (G.present) deg0 = std::max(deg0, G.deg0);
+  const int width = std::max(1, b.search_width);
+  const int hb_def = visited_bits(0, efp, width, deg0);
+  // the caller's table size and drop-test interval are kept; otherwise the
+  // default table and one twice as large, and a drop test every 1, 2 or 4
+  // groups (none of them changes a result)
+  std::vector<int> hbs, vgs;
+  if (b.hash_bits > 0) hbs = {b.hash_bits};
+  else if (hb_def < 15) hbs = {0, hb_def + 1};
+  else hbs = {0};
+  if (b.verify_groups > 0) vgs = {b.verify_groups};
+  else vgs = {1, 2, 4};
   for (int team : {8, 16, 32}) {
     WarpShape ws;
     if (!pick_warp_shape(idx->tdtype, chunks, team, &ws)) continue;
-    for (int rows : {4, 8, 16}) {
+    for (int rows : {4, 8, 16})
+      for (int hb : hbs)
+        for (int vg : vgs) {
+          uhnsw_search_opts c = b;
+          c.query_threads = 32;
+          c.team_lanes = team;
+          c.stage_bytes = rows * idx->d_pad * 4;
+          c.hash_bits = hb;
+          c.verify_groups = vg;
+          cands.push_back(c);
+        }
+  }
+  for (int hb : hbs)
+    for (int vg : vgs) {
       uhnsw_search_opts c = b;
-      c.query_threads = 32;
-      c.team_lanes = team;
-      c.stage_bytes = rows * idx->d_pad * 4;
+      c.query_threads = kBlock;
+      c.team_lanes = 0;
+      c.stage_bytes = 0;
+      c.hash_bits = hb;
+      c.verify_groups = vg;
       cands.push_back(c);
     }
-  }
-  {
-    uhnsw_search_opts c = b;
-    c.query_threads = kBlock;
-    c.team_lanes = 0;
-    c.stage_bytes = 0;
-    cands.push_back(c);
-  }
   int64_t* ids = nullptr;
   float* dist = nullptr;
   cudaError_t e = cudaMalloc(&ids, nq * k * 8);
@@ -1064,9 +1107,10 @@ extern "C" int uhnsw_autotune_save(const uhnsw_index* idx, const char* path) {
   if (!f) return fail(UHNSW_EINVAL, "uhnsw_autotune_save: cannot open %s", path);
   std::lock_guard<std::mutex> lock(const_cast<uhnsw_index*>(idx)->tuned_mu);
   for (const auto& tv : idx->tuned)
-    fprintf(f, "%d %d %lld %lld %d %d %d\n", (int)idx->tdtype, idx->d, (long long)(tv.first >> 16),
-            (long long)(tv.first & 0xffff), tv.second.query_threads, tv.second.team_lanes,
-            tv.second.stage_bytes);
+    fprintf(f, "%d %d %lld %lld %d %d %d %d %d\n", (int)idx->tdtype, idx->d,
+            (long long)(tv.first >> 16), (long long)(tv.first & 0xffff), tv.second.query_threads,
+            tv.second.team_lanes, tv.second.stage_bytes, tv.second.hash_bits,
+            tv.second.verify_groups);
   fclose(f);
   return UHNSW_OK;
 }
@@ -1078,16 +1122,24 @@ extern "C" int uhnsw_autotune_load(uhnsw_index* idx, const char* path) {
   if (!f) return fail(UHNSW_EINVAL, "uhnsw_autotune_load: cannot open %s", path);
   int dt, d, qt, team, stage;
   long long efb, kb;
-  while (fscanf(f, "%d %d %lld %lld %d %d %d", &dt, &d, &efb, &kb, &qt, &team, &stage) == 7) {
+  char line[512];
+  while (fgets(line, sizeof(line), f)) {
+    int hb = 0, vg = 0;
+    const int got = sscanf(line, "%d %d %lld %lld %d %d %d %d %d", &dt, &d, &efb, &kb, &qt, &team,
+                           &stage, &hb, &vg);
+    if (got != 7 && got != 9) continue;
     if (dt != (int)idx->tdtype || d != idx->d) continue;
     if ((qt != 32 && qt != kBlock) || (team != 0 && team != 8 && team != 16 && team != 32) ||
-        stage < 0 || stage > 64 * 1024 || efb < 1 || kb < 1)
+        stage < 0 || stage > 64 * 1024 || efb < 1 || kb < 1 || hb < 0 || hb > 15 || vg < 0 ||
+        vg > 16)
       continue;
     uhnsw_search_opts o;
     std::memset(&o, 0, sizeof(o));
     o.query_threads = qt;
     o.team_lanes = team;
     o.stage_bytes = stage;
+    o.hash_bits = hb;
+    o.verify_groups = vg;
     const int64_t key = (efb << 16) | kb;
     std::lock_guard<std::mutex> lock(idx->tuned_mu);
     bool found = false;

@@ -40,7 +40,8 @@ cudaError_t launch_search(uhnsw_dtype dt, TeamShape sh, const QueryArgs& a, int 
 // Resident blocks per SM of the search kernel for this shape and smem size.
 int search_occupancy(uhnsw_dtype dt, TeamShape sh, int block, size_t smem);
 
-cudaError_t launch_verify(const QueryArgs& a, int block, size_t smem, cudaStream_t st);
+// Verification only, one warp per query (4 per block).
+cudaError_t launch_wverify(const QueryArgs& a, cudaStream_t st);
 
 // Beam buckets of a bucketed persistent search (ascending bounds).
 struct BeamBuckets {

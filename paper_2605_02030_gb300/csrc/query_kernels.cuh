@@ -1,6 +1,5 @@
 // The U-HNSW query kernel: routing, HNSW KnnSearch and L_p verification of
-// one query per thread block (Section 3.1, Algorithm 1), plus the
-// verification-only kernel.
+// one query per thread block (Section 3.1, Algorithm 1).
 //
 // One block owns one query at a time (a persistent block pulls the next query
 // index from a device counter).  Per query:
@@ -87,6 +86,7 @@ struct QueryArgs {
   int32_t stage_bytes;  // warp kernel: per-warp staging buffer for cp.async row copies
   int32_t sb;           // warp kernel: traversal rows staged per batch
   int32_t sv;           // warp kernel: FP32 rows staged per verification batch (multiple of 4)
+  int32_t vgroups;      // verification: 32-dimension groups between two drop tests (>= 1)
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
@@ -116,13 +116,20 @@ __device__ __forceinline__ float query_tau(const QueryArgs& a, int64_t qi) {
   return v != 0.f ? v : 0.92f;
 }
 
+// s^e in FP64, rounded to FP32: the returned distance S^(1/p).  Out of line:
+// it runs a few times per query, and inlined it would take instruction-cache
+// space from the search loop.
+static __device__ __noinline__ float cold_pow(float s, double e) {
+  return (float)pow((double)s, e);
+}
+
 // The distance a direct query returns: the base sum's root S^(1/bp).
 __device__ __forceinline__ float base_root(int metric, float bp, float s) {
   return metric == UHNSW_BASE_L1    ? s
          : metric == UHNSW_BASE_L2  ? sqrtf(s)
          : metric == UHNSW_BASE_L05 ? (float)((double)s * (double)s)
-         : metric == UHNSW_BASE_L15 ? (float)pow((double)s, 1.0 / 1.5)
-                                    : (float)pow((double)s, 1.0 / (double)bp);
+         : metric == UHNSW_BASE_L15 ? cold_pow(s, 1.0 / 1.5)
+                                    : cold_pow(s, 1.0 / (double)bp);
 }
 
 // Dynamic shared-memory carve-up (byte offsets), identical on host and device.
@@ -301,7 +308,8 @@ struct VerifyBufs {
 template <int PM>
 __device__ __forceinline__ bool lp_sum_team(const float* __restrict__ base32, int d, int d_pad,
                                             const float* qs, float p, int32_t id, float thr,
-                                            unsigned tmask, int lane8, float& S, int& groups) {
+                                            unsigned tmask, int lane8, float& S, int& groups,
+                                            int vgroups) {
   const float* row = base32 + (int64_t)id * d_pad;
   float acc = 0.0f;
   const int G = (d + 31) >> 5;
@@ -317,11 +325,12 @@ __device__ __forceinline__ bool lp_sum_team(const float* __restrict__ base32, in
     acc += pow_term<PM>(fabsf(x.y - qq.y), p);
     acc += pow_term<PM>(fabsf(x.z - qq.z), p);
     acc += pow_term<PM>(fabsf(x.w - qq.w), p);
+    groups = g + 1;
+    if (groups % vgroups != 0 && groups != G) continue;  // no drop test after this group
     float tot = acc;
     tot += __shfl_xor_sync(tmask, tot, 1);
     tot += __shfl_xor_sync(tmask, tot, 2);
     tot += __shfl_xor_sync(tmask, tot, 4);
-    groups = g + 1;
     if (tot > thr) return false;
     S = tot;
   }
@@ -342,7 +351,7 @@ __device__ __forceinline__ void verify_wave(const QueryArgs& a, const float* qs,
     float S = 0.f;
     int groups = 0;
     const bool done = lp_sum_team<PM>(a.base32, a.d, a.d_pad, qs, p, id, thr, tmask, lane8, S,
-                                      groups);
+                                      groups, a.vgroups);
     if (lane8 == 0) {
       atomicAdd(&s.np, 1);
       atomicAdd(&s.terms, min(groups * 32, a.d));
@@ -454,7 +463,7 @@ __device__ __forceinline__ void write_verified(const QueryArgs& a, int64_t qi, f
   for (int j = threadIdx.x; j < a.k_max; j += BLOCK) {
     if (j < k && j < s.tn) {
       oid[j] = (int64_t)(vb.ti[cur][j] & kIdMask);
-      od[j] = (float)pow((double)vb.td[cur][j], inv_p);
+      od[j] = cold_pow(vb.td[cur][j], inv_p);
     } else {
       oid[j] = -1;
       od[j] = __int_as_float(0x7f800000);
@@ -740,62 +749,6 @@ __global__ void __launch_bounds__(BLOCK) uhnsw_search_kernel(const QueryArgs a) 
     __syncthreads();
     if (!a.queue_head) break;
   }
-}
-
-// ---------------------------------------------------------------- verification only
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) uhnsw_verify_kernel(const QueryArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ BlockScalars s;
-  const SmemLayout L(a.d_pad, 0, 0, a.cmax, a.k_max, a.vcap);
-  if ((uint32_t)L.total > dynamic_smem_bytes()) {
-    if (threadIdx.x == 0) set_error(a.err, UHNSW_ECAPACITY);
-    return;
-  }
-  const int64_t qi = blockIdx.x;
-  if (qi >= a.nq) return;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const float p = a.p[qi];
-  const int k = a.k_max;
-  if (!(p > 0.f) || !(p <= 2.f)) {
-    write_invalid(a, qi, BLOCK);
-    return;
-  }
-  float* qs = reinterpret_cast<float*>(smem + L.qs);
-  uint32_t* cv = reinterpret_cast<uint32_t*>(smem + L.cv);
-  for (int j = tid; j < a.d_pad; j += BLOCK) qs[j] = j < a.d ? a.q[qi * a.d + j] : 0.f;
-  // ordered compaction of the valid candidate slots
-  int tv = 0;
-  const int32_t* row = a.cand + qi * a.cand_t;
-  for (int b0 = 0; b0 < a.cand_t; b0 += BLOCK) {
-    const int j = b0 + tid;
-    const int32_t v = j < a.cand_t ? row[j] : -1;
-    const bool keep = v >= 0 && v < a.n;
-    const unsigned ball = __ballot_sync(kFull, keep);
-    if (lane == 0) s.ri[warp] = __popc(ball);
-    __syncthreads();
-    int off = tv;
-    for (int w = 0; w < warp; ++w) off += s.ri[w];
-    if (keep) cv[off + __popc(ball & lanemask_lt())] = (uint32_t)v;
-    int tot = 0;
-    for (int w = 0; w < BLOCK / 32; ++w) tot += s.ri[w];
-    tv += tot;
-    __syncthreads();
-  }
-  VerifyBufs vb;
-  vb.td[0] = reinterpret_cast<float*>(smem + L.td0);
-  vb.td[1] = reinterpret_cast<float*>(smem + L.td1);
-  vb.ti[0] = reinterpret_cast<uint32_t*>(smem + L.ti0);
-  vb.ti[1] = reinterpret_cast<uint32_t*>(smem + L.ti1);
-  vb.wd = reinterpret_cast<float*>(smem + L.cd);
-  vb.wi = reinterpret_cast<uint32_t*>(smem + L.ci);
-  vb.sd = reinterpret_cast<float*>(smem + L.sd);
-  vb.si = reinterpret_cast<uint32_t*>(smem + L.si);
-  int vc = 0;
-  const int kappa = a.kappa > 0 ? a.kappa : k;
-  verify_dispatch<BLOCK>(a, qs, p, cv, tv, k, kappa, a.tau, false, vb, s, vc);
-  write_verified<BLOCK>(a, qi, p, k, vb, s, vc);
-  write_stats(a, qi, 0, s.np, s.terms, 0, 0, 0, 0, 0);
 }
 
 }  // namespace uhnsw_dev

@@ -5,12 +5,15 @@
 
 namespace uhnsw_dev {
 
-cudaError_t launch_verify(const QueryArgs& a, int block, size_t smem, cudaStream_t st) {
-  if (block != 128) return cudaErrorInvalidValue;
-  auto kern = uhnsw_verify_kernel<128>;
+cudaError_t launch_wverify(const QueryArgs& a, cudaStream_t st) {
+  const WVerifyLayout L(a.d_pad, a.k_max, a.vcap);
+  constexpr int warps = 4;
+  const size_t smem = (size_t)L.total * warps;
+  auto kern = uhnsw_wverify_kernel<warps>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)a.nq, 128, smem, st>>>(a);
+  const unsigned grid = (unsigned)((a.nq + warps - 1) / warps);
+  kern<<<grid, warps * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 

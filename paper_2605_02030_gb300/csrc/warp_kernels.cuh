@@ -340,11 +340,14 @@ __device__ __forceinline__ float add_terms4(float acc, const float4& x, const fl
 // L_p sum of a staged FP32 row (shared memory) by a team of 8 lanes, with the
 // same grouping and drop test as lp_sum_team.  The p form `pm` selects the
 // term code per 32-dimension group (a uniform branch), so that the
-// verification exists once in the kernel and not once per p form.
+// verification exists once in the kernel and not once per p form: with SQ
+// false the forms p = 1, p = 2 and general p, with SQ true the two square-root
+// forms p = 0.5 and p = 1.5 (a copy of its own, out of line).
+template <bool SQ>
 __device__ __forceinline__ bool lp_sum_team_staged(const float* srow, int d, int d_pad,
                                                    const float* qs, float p, int pm, float thr,
                                                    unsigned tmask, int lane8, float& S,
-                                                   int& groups) {
+                                                   int& groups, int vgroups) {
   float acc = 0.0f;
   const int G = (d + 31) >> 5;
   groups = 0;
@@ -355,18 +358,22 @@ __device__ __forceinline__ bool lp_sum_team_staged(const float* srow, int d, int
       x = *reinterpret_cast<const float4*>(srow + j);
       qq = *reinterpret_cast<const float4*>(qs + j);
     }
-    switch (pm) {
-      case kPOne: acc = add_terms4<kPOne>(acc, x, qq, p); break;
-      case kPTwo: acc = add_terms4<kPTwo>(acc, x, qq, p); break;
-      case kPHalf: acc = add_terms4<kPHalf>(acc, x, qq, p); break;
-      case kPThreeHalves: acc = add_terms4<kPThreeHalves>(acc, x, qq, p); break;
-      default: acc = add_terms4<kPGeneral>(acc, x, qq, p); break;
+    if (SQ) {
+      if (pm == kPHalf) acc = add_terms4<kPHalf>(acc, x, qq, p);
+      else acc = add_terms4<kPThreeHalves>(acc, x, qq, p);
+    } else {
+      switch (pm) {
+        case kPOne: acc = add_terms4<kPOne>(acc, x, qq, p); break;
+        case kPTwo: acc = add_terms4<kPTwo>(acc, x, qq, p); break;
+        default: acc = add_terms4<kPGeneral>(acc, x, qq, p); break;
+      }
     }
+    groups = g + 1;
+    if (groups % vgroups != 0 && groups != G) continue;  // no drop test after this group
     float tot = acc;
     tot += __shfl_xor_sync(tmask, tot, 1);
     tot += __shfl_xor_sync(tmask, tot, 2);
     tot += __shfl_xor_sync(tmask, tot, 4);
-    groups = g + 1;
     if (tot > thr) return false;
     S = tot;
   }
@@ -377,6 +384,7 @@ __device__ __forceinline__ bool lp_sum_team_staged(const float* srow, int d, int
 // staged candidates (8 lanes each) against the running threshold and folds
 // the finished ones into the top-k list.  With fixed_thr set, nothing is
 // dropped (the first K of Algorithm 1).
+template <bool SQ>
 __device__ __forceinline__ void warp_verify_range(const QueryArgs& a, const float* qs, float p,
                                                   int pm, const uint32_t* C, int i0, int i1, int k,
                                                   bool no_drop, unsigned char* stage,
@@ -396,8 +404,8 @@ __device__ __forceinline__ void warp_verify_range(const QueryArgs& a, const floa
       int groups = 0;
       if (r < nb) {
         const float* srow = reinterpret_cast<const float*>(stage) + (size_t)r * a.d_pad;
-        done = lp_sum_team_staged(srow, a.d, a.d_pad, qs, p, pm, no_drop ? kInf : v.thr, tmask,
-                                  lane8, S, groups);
+        done = lp_sum_team_staged<SQ>(srow, a.d, a.d_pad, qs, p, pm, no_drop ? kInf : v.thr,
+                                      tmask, lane8, S, groups, a.vgroups);
       }
       const unsigned leaders = __ballot_sync(kFull, lane8 == 0 && r < nb);
       const unsigned fin = __ballot_sync(kFull, lane8 == 0 && done);
@@ -421,13 +429,141 @@ __device__ __forceinline__ void warp_verify_range(const QueryArgs& a, const floa
   }
 }
 
+// acc + |x - q|^p over one group's four elements, the p form chosen at run
+// time: with SQ false p = 1, p = 2 or general p, with SQ true p = 0.5 or 1.5.
+template <bool SQ>
+__device__ __forceinline__ float add_group(float acc, const float4& x, const float4& q, float p,
+                                           int pm) {
+  if (SQ) return pm == kPHalf ? add_terms4<kPHalf>(acc, x, q, p)
+                              : add_terms4<kPThreeHalves>(acc, x, q, p);
+  switch (pm) {
+    case kPOne: return add_terms4<kPOne>(acc, x, q, p);
+    case kPTwo: return add_terms4<kPTwo>(acc, x, q, p);
+    default: return add_terms4<kPGeneral>(acc, x, q, p);
+  }
+}
+
+// L_p sums of two candidates (ids ida, idb; -1 = none) by one team of 8
+// lanes.  A candidate is tested against thr after every vgroups groups and
+// after its last; *done = finished below thr (S = its sum), *groups = groups
+// accumulated.  Dropped or absent candidates take no further SFU work.
+template <bool SQ>
+__device__ __forceinline__ void lp_sum_pair(const float* __restrict__ base32, int d, int d_pad,
+                                            const float* qs, float p, int pm, int32_t ida, int32_t idb,
+                                            float thr, unsigned tmask, int lane8, int vgroups,
+                                            bool& doneA, float& SA, int& gA, bool& doneB,
+                                            float& SB, int& gB) {
+  const int G = (d + 31) >> 5;
+  bool liveA = ida >= 0, liveB = idb >= 0;
+  float accA = 0.f, accB = 0.f;
+  gA = gB = 0;
+  SA = SB = 0.f;
+  const float* ra = base32 + (int64_t)(ida >= 0 ? ida : 0) * d_pad;
+  const float* rb = base32 + (int64_t)(idb >= 0 ? idb : 0) * d_pad;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int g0 = 0; g0 < G && (liveA || liveB); g0 += 4) {
+    float4 xa[4], xb[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = (g0 + u) * 32 + lane8 * 4;
+      const bool in = g0 + u < G && j < d_pad;
+      xa[u] = (liveA && in) ? __ldg(reinterpret_cast<const float4*>(ra + j)) : z;
+      xb[u] = (liveB && in) ? __ldg(reinterpret_cast<const float4*>(rb + j)) : z;
+    }
+    // (fully unrolled: no break, so that xa / xb stay in registers)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int g = g0 + u;
+      if (g < G) {
+        const int j = g * 32 + lane8 * 4;
+        const float4 qq = j < d_pad ? *reinterpret_cast<const float4*>(qs + j) : z;
+        if (liveA) {
+          accA = add_group<SQ>(accA, xa[u], qq, p, pm);
+          gA = g + 1;
+        }
+        if (liveB) {
+          accB = add_group<SQ>(accB, xb[u], qq, p, pm);
+          gB = g + 1;
+        }
+        if ((g + 1) % vgroups == 0 || g + 1 == G) {
+          float ta = accA, tb = accB;
+          ta += __shfl_xor_sync(tmask, ta, 1);
+          tb += __shfl_xor_sync(tmask, tb, 1);
+          ta += __shfl_xor_sync(tmask, ta, 2);
+          tb += __shfl_xor_sync(tmask, tb, 2);
+          ta += __shfl_xor_sync(tmask, ta, 4);
+          tb += __shfl_xor_sync(tmask, tb, 4);
+          if (liveA) {
+            if (ta > thr) liveA = false;
+            else SA = ta;
+          }
+          if (liveB) {
+            if (tb > thr) liveB = false;
+            else SB = tb;
+          }
+        }
+      }
+    }
+  }
+  doneA = liveA;
+  doneB = liveB;
+}
+
+// Verifies C[i0 .. i1) in waves of 8 candidates (two per team) against the
+// running threshold (none with no_drop) and folds the finished ones into the
+// top-k list.
+template <bool SQ>
+__device__ __forceinline__ void wverify_range(const QueryArgs& a, const float* qs, float p, int pm,
+                                              const uint32_t* C, int i0, int i1, int k,
+                                              bool no_drop, WarpVerify& v) {
+  const int lane = threadIdx.x & 31;
+  const int team = lane >> 3, lane8 = lane & 7;
+  const unsigned tmask = 0xffu << (team * 8);
+  const float kInf = __int_as_float(0x7f800000);
+  for (int s0 = i0; s0 < i1; s0 += 8) {
+    const int ia = s0 + team, ib = s0 + 4 + team;
+    const int32_t ida = ia < i1 ? (int32_t)chk_idx((int64_t)(C[ia] & kIdMask), a.n, 2, a.err) : -1;
+    const int32_t idb = ib < i1 ? (int32_t)chk_idx((int64_t)(C[ib] & kIdMask), a.n, 2, a.err) : -1;
+    bool dA, dB;
+    float SA, SB;
+    int gA, gB;
+    lp_sum_pair<SQ>(a.base32, a.d, a.d_pad, qs, p, pm, ida, idb, no_drop ? kInf : v.thr, tmask,
+                    lane8, a.vgroups, dA, SA, gA, dB, SB, gB);
+    const bool lead = lane8 == 0;
+    v.np += __popc(__ballot_sync(kFull, lead && ida >= 0)) +
+            __popc(__ballot_sync(kFull, lead && idb >= 0));
+    int tg = lead ? (ida >= 0 ? min(gA * 32, a.d) : 0) + (idb >= 0 ? min(gB * 32, a.d) : 0) : 0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) tg += __shfl_xor_sync(kFull, tg, off);
+    v.terms += tg;
+    const unsigned finA = __ballot_sync(kFull, lead && dA);
+    const unsigned finB = __ballot_sync(kFull, lead && dB);
+    if (lead && dA) {
+      const int pos = __popc(finA & lanemask_lt());
+      v.wd[pos] = SA;
+      v.wi[pos] = (uint32_t)ida;
+    }
+    if (lead && dB) {
+      const int pos = __popc(finA) + __popc(finB & lanemask_lt());
+      v.wd[pos] = SB;
+      v.wi[pos] = (uint32_t)idb;
+    }
+    __syncwarp();
+    v.tn = warp_merge(v.cd_(), v.ci_(), v.tn, v.wd, v.wi, __popc(finA) + __popc(finB), v.sd, v.si,
+                      v.nd_(), v.ni_(), k, nullptr);
+    v.cur ^= 1;
+    v.thr = v.tn == k ? v.cd_()[k - 1] : kInf;
+  }
+}
+
 // Exact mode verifies all of C as one range.  Algorithm 1 takes the first K
 // without a drop test, then batches of kappa until the overlap test passes.
-// One call site of warp_verify_range per p form keeps the kernel's code small.
-__device__ __forceinline__ void warp_verify_run(const QueryArgs& a, const float* qs, float p,
-                                                const uint32_t* C, int t, int k, int kappa,
-                                                float tau, bool exact, unsigned char* stage,
-                                                WarpVerify& v) {
+// One call site of warp_verify_range per copy keeps the kernel's code small.
+template <bool SQ>
+__device__ __forceinline__ void warp_verify_run_t(const QueryArgs& a, const float* qs, float p,
+                                                  const uint32_t* C, int t, int k, int kappa,
+                                                  float tau, bool exact, unsigned char* stage,
+                                                  WarpVerify& v) {
   const int lane = threadIdx.x & 31;
   const int pm = pmode_of(p);
   v.tn = 0;
@@ -440,7 +576,7 @@ __device__ __forceinline__ void warp_verify_run(const QueryArgs& a, const float*
       for (int j = lane; j < v.tn; j += 32) v.ci_()[j] |= kExpanded;  // mark R
       __syncwarp();
     }
-    warp_verify_range(a, qs, p, pm, C, i, bend, k, paper && i == 0, stage, v);
+    warp_verify_range<SQ>(a, qs, p, pm, C, i, bend, k, paper && i == 0, stage, v);
     const bool batch = i > 0;
     i = bend;
     if (batch) {
@@ -453,6 +589,19 @@ __device__ __forceinline__ void warp_verify_run(const QueryArgs& a, const float*
       if ((float)ov / (float)k >= tau) break;
     }
   }
+}
+
+// The square-root forms (p = 0.5, 1.5; Section 2.1's fast cases) run a copy
+// of their own; the other forms share one.
+__device__ __forceinline__ void warp_verify_run(const QueryArgs& a, const float* qs, float p,
+                                                const uint32_t* C, int t, int k, int kappa,
+                                                float tau, bool exact, unsigned char* stage,
+                                                WarpVerify& v) {
+  const int pm = pmode_of(p);
+  if (pm == kPHalf || pm == kPThreeHalves)
+    warp_verify_run_t<true>(a, qs, p, C, t, k, kappa, tau, exact, stage, v);
+  else
+    warp_verify_run_t<false>(a, qs, p, C, t, k, kappa, tau, exact, stage, v);
 }
 
 // ---------------------------------------------------------------- one query (warp)
@@ -687,13 +836,135 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
   for (int j = lane; j < a.k_max; j += 32) {
     if (j < k && j < v.tn) {
       oid[j] = (int64_t)(v.ci_()[j] & kIdMask);
-      odist[j] = (float)pow((double)v.cd_()[j], inv_p);
+      odist[j] = cold_pow(v.cd_()[j], inv_p);
     } else {
       oid[j] = -1;
       odist[j] = kInf;
     }
   }
   if (lane == 0) put_stats(a, qi, nb, v.np, v.terms, nexp, nres, 0, rt.slot + 1, nadj);
+}
+
+// ---------------------------------------------------------------- verification only (warp)
+// The verification-only launch (uhnsw_verify, Algorithm 1 lines 6-10 on given
+// candidate lists): one warp per query, no block-wide barrier.  Each 8-lane
+// team takes two candidates at once and reads their FP32 rows four
+// 32-dimension groups at a time into registers, all loads of a block issued
+// before any arithmetic, so that the SFU work of one candidate overlaps the
+// other's reductions and the next block's loads.  Every lane sums the same
+// elements in the same order as lp_sum_team (element j = 32 g + 4 lane + e),
+// so the sums are bit-identical to the block kernel's.
+
+// Shared-memory carve-up of one warp of the verification-only kernel.
+struct WVerifyLayout {
+  int qs, td0, ti0, td1, ti1, wd, wi, sd, si, cv, total;
+  __host__ __device__ WVerifyLayout(int d_pad, int k_max, int vcap) {
+    int o = 0;
+    qs = o; o += align16(d_pad * 4);
+    td0 = o; o += align16(k_max * 4);
+    ti0 = o; o += align16(k_max * 4);
+    td1 = o; o += align16(k_max * 4);
+    ti1 = o; o += align16(k_max * 4);
+    wd = o; o += align16(8 * 4);
+    wi = o; o += align16(8 * 4);
+    sd = o; o += align16(8 * 4);
+    si = o; o += align16(8 * 4);
+    cv = o; o += align16(vcap * 4);
+    total = o;
+  }
+};
+
+// Exact mode over all of C, or Algorithm 1's first K then batches of kappa.
+template <bool SQ>
+__device__ __forceinline__ void wverify_run(const QueryArgs& a, const float* qs, float p, int pm,
+                                            const uint32_t* C, int t, int k, WarpVerify& v) {
+  const int lane = threadIdx.x & 31;
+  v.tn = 0;
+  v.thr = __int_as_float(0x7f800000);
+  if (a.mode != UHNSW_VERIFY_PAPER) {
+    wverify_range<SQ>(a, qs, p, pm, C, 0, t, k, false, v);
+    return;
+  }
+  const int kappa = a.kappa > 0 ? a.kappa : k;
+  const int n0 = min(k, t);
+  wverify_range<SQ>(a, qs, p, pm, C, 0, n0, k, true, v);
+  for (int i = n0; i < t;) {
+    const int bend = min(i + kappa, t);
+    for (int j = lane; j < v.tn; j += 32) v.ci_()[j] |= kExpanded;  // mark R
+    __syncwarp();
+    wverify_range<SQ>(a, qs, p, pm, C, i, bend, k, false, v);
+    i = bend;
+    int ov = 0;
+    for (int j = lane; j < v.tn; j += 32) ov += (int)(v.ci_()[j] >> 31);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) ov += __shfl_xor_sync(kFull, ov, off);
+    for (int j = lane; j < v.tn; j += 32) v.ci_()[j] &= kIdMask;
+    __syncwarp();
+    if ((float)ov / (float)k >= a.tau) break;
+  }
+}
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) uhnsw_wverify_kernel(const QueryArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const WVerifyLayout L(a.d_pad, a.k_max, a.vcap);
+  constexpr int warps = WARPS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if ((uint32_t)(L.total * warps) > dynamic_smem_bytes()) {
+    if (threadIdx.x == 0) set_error(a.err, UHNSW_ECAPACITY);
+    return;
+  }
+  const int64_t qi = (int64_t)blockIdx.x * warps + warp;
+  if (qi >= a.nq) return;
+  unsigned char* ws = smem + (size_t)warp * L.total;
+  const float p = a.p[qi];
+  const int k = a.k_max;
+  int64_t* oid = a.out_ids + qi * a.k_max;
+  float* od = a.out_dist + qi * a.k_max;
+  const float kInf = __int_as_float(0x7f800000);
+  if (!(p > 0.f) || !(p <= 2.f)) {
+    for (int j = lane; j < k; j += 32) {
+      oid[j] = -1;
+      od[j] = kInf;
+    }
+    if (lane == 0) put_stats(a, qi, 0, 0, 0, 0, 0, UHNSW_EINVAL, 0, 0);
+    return;
+  }
+  float* qs = reinterpret_cast<float*>(ws + L.qs);
+  uint32_t* cv = reinterpret_cast<uint32_t*>(ws + L.cv);
+  for (int j = lane; j < a.d_pad; j += 32) qs[j] = j < a.d ? a.q[qi * a.d + j] : 0.f;
+  // the valid candidate slots, in order
+  int tv = 0;
+  const int32_t* row = a.cand + qi * a.cand_t;
+  for (int b0 = 0; b0 < a.cand_t; b0 += 32) {
+    const int j = b0 + lane;
+    const int32_t c = j < a.cand_t ? row[j] : -1;
+    warp_append(c >= 0 && c < a.n, (uint32_t)c, cv, tv, a.vcap, a.err);
+  }
+  __syncwarp();
+  WarpVerify v;
+  v.td[0] = reinterpret_cast<float*>(ws + L.td0);
+  v.td[1] = reinterpret_cast<float*>(ws + L.td1);
+  v.ti[0] = reinterpret_cast<uint32_t*>(ws + L.ti0);
+  v.ti[1] = reinterpret_cast<uint32_t*>(ws + L.ti1);
+  v.wd = reinterpret_cast<float*>(ws + L.wd);
+  v.wi = reinterpret_cast<uint32_t*>(ws + L.wi);
+  v.sd = reinterpret_cast<float*>(ws + L.sd);
+  v.si = reinterpret_cast<uint32_t*>(ws + L.si);
+  const int pm = pmode_of(p);
+  if (pm == kPHalf || pm == kPThreeHalves) wverify_run<true>(a, qs, p, pm, cv, tv, k, v);
+  else wverify_run<false>(a, qs, p, pm, cv, tv, k, v);
+  const double inv_p = 1.0 / (double)p;
+  for (int j = lane; j < k; j += 32) {
+    if (j < v.tn) {
+      oid[j] = (int64_t)(v.ci_()[j] & kIdMask);
+      od[j] = (float)pow((double)v.cd_()[j], inv_p);  // inline: a call here costs spills
+    } else {
+      oid[j] = -1;
+      od[j] = kInf;
+    }
+  }
+  if (lane == 0) put_stats(a, qi, 0, v.np, v.terms, 0, 0, 0, 0, 0);
 }
 
 // WARPS independent queries per block; a.queue_head set = persistent (each

@@ -73,6 +73,8 @@ class _SearchOpts(C.Structure):
         ("kernel_events", C.c_void_p),
         ("t_per_query", C.c_void_p),
         ("tau_per_query", C.c_void_p),
+        ("hash_bits", C.c_int32),
+        ("verify_groups", C.c_int32),
     ]
 
 
@@ -328,7 +330,7 @@ class Index:
     # -- helpers
     def _opts(self, t=0, kappa=0, tau=0.0, cutoff=0.0, mode="exact", width=1, persistent=False,
               use_graph=False, ef_max=0, stats_t=None, query_threads=0, stage_bytes=0,
-              team_lanes=0):
+              team_lanes=0, hash_bits=0, verify_groups=0):
         o = _SearchOpts()
         o.t, o.kappa, o.tau, o.cutoff = int(t), int(kappa), float(tau), float(cutoff)
         o.verify_mode = MODES[mode] if isinstance(mode, str) else int(mode)
@@ -339,6 +341,8 @@ class Index:
         o.query_threads = int(query_threads)
         o.stage_bytes = int(stage_bytes)
         o.team_lanes = int(team_lanes)
+        o.hash_bits = int(hash_bits)
+        o.verify_groups = int(verify_groups)
         o.stats = stats_t.data_ptr() if stats_t is not None else None
         return o
 
@@ -346,6 +350,7 @@ class Index:
                kappa: int = 0, cutoff: float = 0.0, mode: str = "exact", width: int = 1,
                persistent: bool = False, use_graph: bool = False, ef_max: int = 0,
                query_threads: int = 0, stage_bytes: int = 0, team_lanes: int = 0,
+               hash_bits: int = 0, verify_groups: int = 0,
                stats: bool = False, out=None, stream=None, kernel_events=None):
         """Algorithm 1 on device tensors.  q: float32 [nq, d] cuda; p: float32 [nq];
         k / ef / t: int (same for all) or int32 [nq] tensors; tau: float or
@@ -374,7 +379,7 @@ class Index:
         tau_t = tau if torch.is_tensor(tau) else None
         o = self._opts(0 if t_t is not None else t, kappa, 0.0 if tau_t is not None else tau,
                        cutoff, mode, width, persistent, use_graph, ef_max, st, query_threads,
-                       stage_bytes, team_lanes)
+                       stage_bytes, team_lanes, hash_bits, verify_groups)
         o.t_per_query = t_t.data_ptr() if t_t is not None else None
         o.tau_per_query = tau_t.data_ptr() if tau_t is not None else None
         if kernel_events is not None:
@@ -412,7 +417,8 @@ class Index:
                  if isinstance(kw.get("tau"), np.ndarray) else None)
         o = self._opts(**{x: kw[x] for x in ("t", "kappa", "tau", "cutoff", "mode", "width",
                                              "persistent", "ef_max", "query_threads",
-                                             "stage_bytes", "team_lanes") if x in kw})
+                                             "stage_bytes", "team_lanes", "hash_bits",
+                                             "verify_groups") if x in kw})
         o.t_per_query = t_a.ctypes.data if t_a is not None else None
         o.tau_per_query = tau_a.ctypes.data if tau_a is not None else None
         _check(lib.uhnsw_search_host(self._h, _np_ptr(q), _np_ptr(p), _np_ptr(k_a), _np_ptr(ef_a),
@@ -421,7 +427,7 @@ class Index:
         return ids, dist
 
     def verify(self, q, p, cand, k: int, *, mode: str = "exact", kappa: int = 0, tau: float = 0.0,
-               stats: bool = False, stream=None):
+               verify_groups: int = 0, stats: bool = False, stream=None):
         """Verification only on candidate lists cand int32 [nq, t] (-1 = absent)."""
         import torch
         lib = load_library()
@@ -429,7 +435,7 @@ class Index:
         ids = torch.empty((nq, k), dtype=torch.int64, device=q.device)
         dist = torch.empty((nq, k), dtype=torch.float32, device=q.device)
         st = torch.zeros((nq, NSTATS), dtype=torch.int32, device=q.device) if stats else None
-        o = self._opts(kappa=kappa, tau=tau, mode=mode, stats_t=st)
+        o = self._opts(kappa=kappa, tau=tau, mode=mode, stats_t=st, verify_groups=verify_groups)
         _check(lib.uhnsw_verify(self._h, _t_ptr(q), _t_ptr(p), _t_ptr(cand), t, k, nq, C.byref(o),
                                 _t_ptr(ids), _t_ptr(dist), _stream_ptr(stream)))
         return ids, dist, st
@@ -465,7 +471,8 @@ class Index:
         _check(lib.uhnsw_autotune(self._h, _t_ptr(q), _t_ptr(p), q.shape[0], int(k), int(ef),
                                   C.byref(b), _stream_ptr(stream), C.byref(best), C.byref(ms)))
         return ({"query_threads": best.query_threads, "team_lanes": best.team_lanes,
-                 "stage_bytes": best.stage_bytes}, ms.value)
+                 "stage_bytes": best.stage_bytes, "hash_bits": best.hash_bits,
+                 "verify_groups": best.verify_groups}, ms.value)
 
     def autotune_save(self, path: str):
         _check(load_library().uhnsw_autotune_save(self._h, path.encode()))

@@ -346,6 +346,7 @@ def test_autotune_picks_a_valid_configuration(U, search_case, tmp_path):
     assert best["query_threads"] in (32, 128) and ms > 0
     if best["query_threads"] == 32:
         assert best["team_lanes"] in (8, 16, 32) and best["stage_bytes"] % (4 * w.d) == 0
+    assert best["verify_groups"] in (1, 2, 4) and best["hash_bits"] >= 0
     tuned = idx.search(q, pp, k=10, ef=40)
     explicit = idx.search(q, pp, k=10, ef=40, **best)
     torch.cuda.synchronize()
@@ -353,7 +354,8 @@ def test_autotune_picks_a_valid_configuration(U, search_case, tmp_path):
     path = str(tmp_path / "tuned.txt")
     idx.autotune_save(path)
     line = open(path).read().split()
-    assert len(line) == 7 and int(line[1]) == w.d and int(line[4]) == best["query_threads"]
+    assert len(line) == 9 and int(line[1]) == w.d and int(line[4]) == best["query_threads"]
+    assert int(line[7]) == best["hash_bits"] and int(line[8]) == best["verify_groups"]
     idx2 = U.Index(base, g1, g2, traverse_dtype="f16")
     idx2.autotune_load(path)
     again = idx2.search(q, pp, k=10, ef=40)
@@ -361,6 +363,42 @@ def test_autotune_picks_a_valid_configuration(U, search_case, tmp_path):
     assert torch.equal(again[0], tuned[0]) and torch.equal(again[1], tuned[1])
     idx.close()
     idx2.close()
+
+
+def test_table_size_and_drop_interval_change_no_result(U, search_case, qt):
+    """The autotuner's visited-table size and drop-test interval leave every
+    sum and decision of the search unchanged: any allowed table size (from
+    the smallest that holds a beam plus one step of candidates) and a drop
+    test every 1 to 5 verification groups return the default call's ids and
+    distances bit for bit, in both verification modes, and so does the
+    verification-only entry point.  A table below the minimum is refused."""
+    import math
+
+    cname, w, base, qs, p, g1, g2 = search_case
+    idx = U.Index(base, g1, g2, traverse_dtype="f32")
+    q, pp = dev(qs), dev(p)
+    ef, width = 40, 2
+    m0 = max(g1["max_degree0"], g2["max_degree0"])
+    lo = math.ceil(math.log2(2 * (ef + width * m0)))
+    for mode in ("exact", "paper"):
+        ref = idx.search(q, pp, k=10, ef=ef, width=width, mode=mode, query_threads=qt)
+        for hb in (lo, lo + 1, lo + 2):
+            for vg in (1, 2, 3, 5):
+                got = idx.search(q, pp, k=10, ef=ef, width=width, mode=mode, query_threads=qt,
+                                 hash_bits=hb, verify_groups=vg)
+                torch.cuda.synchronize()
+                assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1]), (mode, hb, vg)
+    with pytest.raises(U.UHNSWError):
+        idx.search(q, pp, k=10, ef=ef, width=width, query_threads=qt, hash_bits=lo - 1)
+    cand = torch.from_numpy(np.stack([np.random.default_rng(i).choice(len(base), 60, replace=False)
+                                      for i in range(len(qs))]).astype(np.int32)).cuda()
+    vref = idx.verify(q, pp, cand, 10)
+    for vg in (2, 4, 16):
+        got = idx.verify(q, pp, cand, 10, verify_groups=vg)
+        torch.cuda.synchronize()
+        assert torch.equal(got[0], vref[0]) and torch.equal(got[1], vref[1])
+    assert idx.device_status() == 0
+    idx.close()
 
 
 def test_bucketed_persistent_queue_matches_plain(U, search_case, qt):
