@@ -177,12 +177,14 @@ typedef struct {
                             and refilled with the beam, which cannot change the beam); a
                             smaller table re-evaluates more nodes, a larger one takes
                             shared memory from other queries. */
-  int32_t verify_groups; /* verification: 32-dimension groups accumulated between two
-                            tests of a candidate's partial sum against the running k-th
-                            best sum, 1..16; 0 => 1.  Every lane accumulates its elements
-                            in the same order whatever the value, so sums and results do
-                            not depend on it; it trades drop-test work for candidates
-                            summed further before they are dropped. */
+  int32_t verify_groups; /* verification in the warp-per-query kernels: 32-dimension
+                            groups accumulated between two tests of a candidate's partial
+                            sum against the running k-th best sum, 1..16; 0 => 1 (the
+                            block-per-query kernel tests after every group).  Every lane
+                            accumulates its elements in the same order whatever the
+                            value, so sums and results do not depend on it; it trades
+                            drop-test work for candidates summed further before they are
+                            dropped. */
 } uhnsw_search_opts;
 
 /*
@@ -336,7 +338,7 @@ int uhnsw_exact_static(uhnsw_index* idx, const float* q, const float* p, int64_t
  * kernel with each compiled team width that covers a row (8, 16, 32 lanes),
  * 4, 8 or 16 staged verification rows, the default visited table or one
  * twice its size, and a drop test every 1, 2 or 4 verification groups; the
- * block-per-query kernel.  The candidates run the same algorithm in the same
+ * block-per-query kernel with either table size.  The candidates run the same algorithm in the same
  * order; their distances can differ only by the FP32 summation order of the
  * team width (table size, staging and drop-test interval change no sum).
  * hash_bits and verify_groups set in `base` are kept, not searched.  `base` supplies the other options

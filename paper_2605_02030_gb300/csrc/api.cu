@@ -1030,16 +1030,14 @@ extern "C" int uhnsw_autotune(uhnsw_index* idx, const float* q, const float* p, 
           cands.push_back(c);
         }
   }
-  for (int hb : hbs)
-    for (int vg : vgs) {
-      uhnsw_search_opts c = b;
-      c.query_threads = kBlock;
-      c.team_lanes = 0;
-      c.stage_bytes = 0;
-      c.hash_bits = hb;
-      c.verify_groups = vg;
-      cands.push_back(c);
-    }
+  for (int hb : hbs) {  // (the block kernel tests after every group: no interval to try)
+    uhnsw_search_opts c = b;
+    c.query_threads = kBlock;
+    c.team_lanes = 0;
+    c.stage_bytes = 0;
+    c.hash_bits = hb;
+    cands.push_back(c);
+  }
   int64_t* ids = nullptr;
   float* dist = nullptr;
   cudaError_t e = cudaMalloc(&ids, nq * k * 8);

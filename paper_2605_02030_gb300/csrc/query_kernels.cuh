@@ -86,7 +86,8 @@ struct QueryArgs {
   int32_t stage_bytes;  // warp kernel: per-warp staging buffer for cp.async row copies
   int32_t sb;           // warp kernel: traversal rows staged per batch
   int32_t sv;           // warp kernel: FP32 rows staged per verification batch (multiple of 4)
-  int32_t vgroups;      // verification: 32-dimension groups between two drop tests (>= 1)
+  int32_t vgroups;      // warp kernels' verification: 32-dimension groups between two drop
+                        // tests (>= 1); the block kernel tests after every group
 };
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
@@ -116,20 +117,13 @@ __device__ __forceinline__ float query_tau(const QueryArgs& a, int64_t qi) {
   return v != 0.f ? v : 0.92f;
 }
 
-// s^e in FP64, rounded to FP32: the returned distance S^(1/p).  Out of line:
-// it runs a few times per query, and inlined it would take instruction-cache
-// space from the search loop.
-static __device__ __noinline__ float cold_pow(float s, double e) {
-  return (float)pow((double)s, e);
-}
-
 // The distance a direct query returns: the base sum's root S^(1/bp).
 __device__ __forceinline__ float base_root(int metric, float bp, float s) {
   return metric == UHNSW_BASE_L1    ? s
          : metric == UHNSW_BASE_L2  ? sqrtf(s)
          : metric == UHNSW_BASE_L05 ? (float)((double)s * (double)s)
-         : metric == UHNSW_BASE_L15 ? cold_pow(s, 1.0 / 1.5)
-                                    : cold_pow(s, 1.0 / (double)bp);
+         : metric == UHNSW_BASE_L15 ? (float)pow((double)s, 1.0 / 1.5)
+                                    : (float)pow((double)s, 1.0 / (double)bp);
 }
 
 // Dynamic shared-memory carve-up (byte offsets), identical on host and device.
@@ -308,8 +302,7 @@ struct VerifyBufs {
 template <int PM>
 __device__ __forceinline__ bool lp_sum_team(const float* __restrict__ base32, int d, int d_pad,
                                             const float* qs, float p, int32_t id, float thr,
-                                            unsigned tmask, int lane8, float& S, int& groups,
-                                            int vgroups) {
+                                            unsigned tmask, int lane8, float& S, int& groups) {
   const float* row = base32 + (int64_t)id * d_pad;
   float acc = 0.0f;
   const int G = (d + 31) >> 5;
@@ -325,12 +318,11 @@ __device__ __forceinline__ bool lp_sum_team(const float* __restrict__ base32, in
     acc += pow_term<PM>(fabsf(x.y - qq.y), p);
     acc += pow_term<PM>(fabsf(x.z - qq.z), p);
     acc += pow_term<PM>(fabsf(x.w - qq.w), p);
-    groups = g + 1;
-    if (groups % vgroups != 0 && groups != G) continue;  // no drop test after this group
     float tot = acc;
     tot += __shfl_xor_sync(tmask, tot, 1);
     tot += __shfl_xor_sync(tmask, tot, 2);
     tot += __shfl_xor_sync(tmask, tot, 4);
+    groups = g + 1;
     if (tot > thr) return false;
     S = tot;
   }
@@ -351,7 +343,7 @@ __device__ __forceinline__ void verify_wave(const QueryArgs& a, const float* qs,
     float S = 0.f;
     int groups = 0;
     const bool done = lp_sum_team<PM>(a.base32, a.d, a.d_pad, qs, p, id, thr, tmask, lane8, S,
-                                      groups, a.vgroups);
+                                      groups);
     if (lane8 == 0) {
       atomicAdd(&s.np, 1);
       atomicAdd(&s.terms, min(groups * 32, a.d));
@@ -463,7 +455,7 @@ __device__ __forceinline__ void write_verified(const QueryArgs& a, int64_t qi, f
   for (int j = threadIdx.x; j < a.k_max; j += BLOCK) {
     if (j < k && j < s.tn) {
       oid[j] = (int64_t)(vb.ti[cur][j] & kIdMask);
-      od[j] = cold_pow(vb.td[cur][j], inv_p);
+      od[j] = (float)pow((double)vb.td[cur][j], inv_p);
     } else {
       oid[j] = -1;
       od[j] = __int_as_float(0x7f800000);

@@ -340,10 +340,7 @@ __device__ __forceinline__ float add_terms4(float acc, const float4& x, const fl
 // L_p sum of a staged FP32 row (shared memory) by a team of 8 lanes, with the
 // same grouping and drop test as lp_sum_team.  The p form `pm` selects the
 // term code per 32-dimension group (a uniform branch), so that the
-// verification exists once in the kernel and not once per p form: with SQ
-// false the forms p = 1, p = 2 and general p, with SQ true the two square-root
-// forms p = 0.5 and p = 1.5 (a copy of its own, out of line).
-template <bool SQ>
+// verification exists once in the kernel and not once per p form.
 __device__ __forceinline__ bool lp_sum_team_staged(const float* srow, int d, int d_pad,
                                                    const float* qs, float p, int pm, float thr,
                                                    unsigned tmask, int lane8, float& S,
@@ -351,6 +348,7 @@ __device__ __forceinline__ bool lp_sum_team_staged(const float* srow, int d, int
   float acc = 0.0f;
   const int G = (d + 31) >> 5;
   groups = 0;
+  int until_test = vgroups;
   for (int g = 0; g < G; ++g) {
     const int j = g * 32 + lane8 * 4;
     float4 x = make_float4(0.f, 0.f, 0.f, 0.f), qq = x;
@@ -358,18 +356,16 @@ __device__ __forceinline__ bool lp_sum_team_staged(const float* srow, int d, int
       x = *reinterpret_cast<const float4*>(srow + j);
       qq = *reinterpret_cast<const float4*>(qs + j);
     }
-    if (SQ) {
-      if (pm == kPHalf) acc = add_terms4<kPHalf>(acc, x, qq, p);
-      else acc = add_terms4<kPThreeHalves>(acc, x, qq, p);
-    } else {
-      switch (pm) {
-        case kPOne: acc = add_terms4<kPOne>(acc, x, qq, p); break;
-        case kPTwo: acc = add_terms4<kPTwo>(acc, x, qq, p); break;
-        default: acc = add_terms4<kPGeneral>(acc, x, qq, p); break;
-      }
+    switch (pm) {
+      case kPOne: acc = add_terms4<kPOne>(acc, x, qq, p); break;
+      case kPTwo: acc = add_terms4<kPTwo>(acc, x, qq, p); break;
+      case kPHalf: acc = add_terms4<kPHalf>(acc, x, qq, p); break;
+      case kPThreeHalves: acc = add_terms4<kPThreeHalves>(acc, x, qq, p); break;
+      default: acc = add_terms4<kPGeneral>(acc, x, qq, p); break;
     }
     groups = g + 1;
-    if (groups % vgroups != 0 && groups != G) continue;  // no drop test after this group
+    if (--until_test > 0 && groups != G) continue;  // no drop test after this group
+    until_test = vgroups;
     float tot = acc;
     tot += __shfl_xor_sync(tmask, tot, 1);
     tot += __shfl_xor_sync(tmask, tot, 2);
@@ -384,7 +380,6 @@ __device__ __forceinline__ bool lp_sum_team_staged(const float* srow, int d, int
 // staged candidates (8 lanes each) against the running threshold and folds
 // the finished ones into the top-k list.  With fixed_thr set, nothing is
 // dropped (the first K of Algorithm 1).
-template <bool SQ>
 __device__ __forceinline__ void warp_verify_range(const QueryArgs& a, const float* qs, float p,
                                                   int pm, const uint32_t* C, int i0, int i1, int k,
                                                   bool no_drop, unsigned char* stage,
@@ -404,8 +399,8 @@ __device__ __forceinline__ void warp_verify_range(const QueryArgs& a, const floa
       int groups = 0;
       if (r < nb) {
         const float* srow = reinterpret_cast<const float*>(stage) + (size_t)r * a.d_pad;
-        done = lp_sum_team_staged<SQ>(srow, a.d, a.d_pad, qs, p, pm, no_drop ? kInf : v.thr,
-                                      tmask, lane8, S, groups, a.vgroups);
+        done = lp_sum_team_staged(srow, a.d, a.d_pad, qs, p, pm, no_drop ? kInf : v.thr, tmask,
+                                  lane8, S, groups, a.vgroups);
       }
       const unsigned leaders = __ballot_sync(kFull, lane8 == 0 && r < nb);
       const unsigned fin = __ballot_sync(kFull, lane8 == 0 && done);
@@ -456,6 +451,7 @@ __device__ __forceinline__ void lp_sum_pair(const float* __restrict__ base32, in
   const int G = (d + 31) >> 5;
   bool liveA = ida >= 0, liveB = idb >= 0;
   float accA = 0.f, accB = 0.f;
+  int until_test = vgroups;
   gA = gB = 0;
   SA = SB = 0.f;
   const float* ra = base32 + (int64_t)(ida >= 0 ? ida : 0) * d_pad;
@@ -485,7 +481,8 @@ __device__ __forceinline__ void lp_sum_pair(const float* __restrict__ base32, in
           accB = add_group<SQ>(accB, xb[u], qq, p, pm);
           gB = g + 1;
         }
-        if ((g + 1) % vgroups == 0 || g + 1 == G) {
+        if (--until_test == 0 || g + 1 == G) {
+          until_test = vgroups;
           float ta = accA, tb = accB;
           ta += __shfl_xor_sync(tmask, ta, 1);
           tb += __shfl_xor_sync(tmask, tb, 1);
@@ -558,12 +555,12 @@ __device__ __forceinline__ void wverify_range(const QueryArgs& a, const float* q
 
 // Exact mode verifies all of C as one range.  Algorithm 1 takes the first K
 // without a drop test, then batches of kappa until the overlap test passes.
-// One call site of warp_verify_range per copy keeps the kernel's code small.
-template <bool SQ>
-__device__ __forceinline__ void warp_verify_run_t(const QueryArgs& a, const float* qs, float p,
-                                                  const uint32_t* C, int t, int k, int kappa,
-                                                  float tau, bool exact, unsigned char* stage,
-                                                  WarpVerify& v) {
+// One call site of warp_verify_range for every p form keeps the kernel's code
+// small.
+__device__ __forceinline__ void warp_verify_run(const QueryArgs& a, const float* qs, float p,
+                                                const uint32_t* C, int t, int k, int kappa,
+                                                float tau, bool exact, unsigned char* stage,
+                                                WarpVerify& v) {
   const int lane = threadIdx.x & 31;
   const int pm = pmode_of(p);
   v.tn = 0;
@@ -576,7 +573,7 @@ __device__ __forceinline__ void warp_verify_run_t(const QueryArgs& a, const floa
       for (int j = lane; j < v.tn; j += 32) v.ci_()[j] |= kExpanded;  // mark R
       __syncwarp();
     }
-    warp_verify_range<SQ>(a, qs, p, pm, C, i, bend, k, paper && i == 0, stage, v);
+    warp_verify_range(a, qs, p, pm, C, i, bend, k, paper && i == 0, stage, v);
     const bool batch = i > 0;
     i = bend;
     if (batch) {
@@ -589,19 +586,6 @@ __device__ __forceinline__ void warp_verify_run_t(const QueryArgs& a, const floa
       if ((float)ov / (float)k >= tau) break;
     }
   }
-}
-
-// The square-root forms (p = 0.5, 1.5; Section 2.1's fast cases) run a copy
-// of their own; the other forms share one.
-__device__ __forceinline__ void warp_verify_run(const QueryArgs& a, const float* qs, float p,
-                                                const uint32_t* C, int t, int k, int kappa,
-                                                float tau, bool exact, unsigned char* stage,
-                                                WarpVerify& v) {
-  const int pm = pmode_of(p);
-  if (pm == kPHalf || pm == kPThreeHalves)
-    warp_verify_run_t<true>(a, qs, p, C, t, k, kappa, tau, exact, stage, v);
-  else
-    warp_verify_run_t<false>(a, qs, p, C, t, k, kappa, tau, exact, stage, v);
 }
 
 // ---------------------------------------------------------------- one query (warp)
@@ -836,7 +820,7 @@ __device__ void warp_query(const QueryArgs& a, int64_t qi, unsigned char* ws, co
   for (int j = lane; j < a.k_max; j += 32) {
     if (j < k && j < v.tn) {
       oid[j] = (int64_t)(v.ci_()[j] & kIdMask);
-      odist[j] = cold_pow(v.cd_()[j], inv_p);
+      odist[j] = (float)pow((double)v.cd_()[j], inv_p);
     } else {
       oid[j] = -1;
       odist[j] = kInf;

@@ -346,7 +346,10 @@ def test_autotune_picks_a_valid_configuration(U, search_case, tmp_path):
     assert best["query_threads"] in (32, 128) and ms > 0
     if best["query_threads"] == 32:
         assert best["team_lanes"] in (8, 16, 32) and best["stage_bytes"] % (4 * w.d) == 0
-    assert best["verify_groups"] in (1, 2, 4) and best["hash_bits"] >= 0
+    # the drop-test interval is searched for the warp kernel only (the block
+    # kernel tests after every group)
+    assert best["verify_groups"] in ((1, 2, 4) if best["query_threads"] == 32 else (0,))
+    assert best["hash_bits"] >= 0
     tuned = idx.search(q, pp, k=10, ef=40)
     explicit = idx.search(q, pp, k=10, ef=40, **best)
     torch.cuda.synchronize()
