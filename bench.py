@@ -471,6 +471,12 @@ def run_ours(args, log):
         except (OSError, ValueError):
             pass
 
+    # the verification kernel alone against the SFU rate measured on this device
+    vroof = verify_roofline(idx32 if idx32 is not None else idx16, q_dev, w,
+                            max(5, args.steps // 2), args.warmup)
+    log(f"verification alone: {vroof['achieved']} of {vroof['peak']} T SFU ops/s "
+        f"({vroof['frac']})")
+
     # end to end through the public C ABI with host buffers (copies inside the timed region)
     pin_q = torch.from_numpy(qs).pin_memory().numpy()
     pin_p = torch.from_numpy(p).pin_memory().numpy()
@@ -610,6 +616,7 @@ def run_ours(args, log):
                                          "search-kernel launch, mean of %d launches after an "
                                          "L2 flush" % len(kern_ms),
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+        "verify_roofline": vroof,
         "e2e": {"value": round(e2e_val, 1), "unit": UNIT,
                 "h2d_bytes_per_step": int(qs.nbytes + p.nbytes),
                 "d2h_bytes_per_step": int(w.nq * k * 12), "recall_at_10": round(e2e_recall, 4),
@@ -624,11 +631,23 @@ def run_ours(args, log):
         # width-1 calibration's ef
         ef1 = next((c["ef"] for c in head["calibration"] if c["width"] == 1), head["ef"])
         line["cpu_baseline"] = cpu_baseline(w, base, qs, p, g1, g2, ef1, k, args.cpu_seconds)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     if idx32 is not None:
         idx32.close()
     idx16.close()
+    if world == 1 and not args.no_extras:
+        # the batched form on the GIST-shaped workload and the serving form on
+        # the 10M unit-vector workload, each at its full size; a failure there
+        # is recorded and leaves the headline line intact
+        del flush, out_ids, out_d, q_dev, cq_dev
+        line["extras"] = {}
+        for name in args.extras.split(","):
+            try:
+                line["extras"][name] = workload_record(args, log, name)
+            except Exception as e:  # noqa: BLE001 - recorded in the line
+                line["extras"][name] = {"error": f"{type(e).__name__}: {e}"[:400]}
+            torch.cuda.empty_cache()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -678,27 +697,36 @@ def _launches_per_call(ef_cap):
 
 
 def run_workload(args, log):
+    """One JSON line for the workload named by --workload."""
+    import torch
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    print(json.dumps(workload_record(args, log, args.workload, sized=True)), flush=True)
+
+
+def workload_record(args, log, name, sized=False):
     """The batched form on the GIST-shaped 1M x 960 workload (BF16 rows, each
-    query with its own p, k and ef), or the serving form on the 10M x 96
-    unit-vector workload (FP16 rows, Poisson arrivals, k in {10, 50})."""
+    query with its own p, k and ef), the serving form on the 10M x 96
+    unit-vector workload (FP16 rows, Poisson arrivals, k in {10, 50}), or
+    U-HNSW-E on the SIFT-shaped base: the record of one run (--n / --nq
+    apply when `sized`)."""
     import torch
     import paper_2605_02030_gb300 as pkg
     from paper_2605_02030_gb300 import uhnsw as U
 
-    rank, local_rank, world = dist_env()
-    torch.cuda.set_device(local_rank)
     pkg.build()
-    w = I.WORKLOADS[args.workload]
-    if args.n:
+    w = I.WORKLOADS[name]
+    if sized and args.n:
         w = w.scaled(n=args.n)
-    if args.nq:
+    if sized and args.nq:
         w = w.scaled(nq=args.nq)
     t0 = time.time()
     base = I.base_vectors(w)
     qs = I.query_vectors(w)
     p, kq, efq = I.query_params(w)
     log(f"inputs {w.n}x{w.d}, {w.nq} queries in {time.time() - t0:.1f} s")
-    g1, g2 = graphs_for(w, base, log, device="cpu" if args.workload == "sift1m_e" else "gpu")
+    g1, g2 = graphs_for(w, base, log, device="cpu" if name == "sift1m_e" else "gpu")
     idx = U.Index(base, g1, g2, traverse_dtype=w.traverse_dtype, metrics=w.metrics)
     q_dev = torch.from_numpy(qs).cuda()
     p_dev = torch.from_numpy(p).cuda()
@@ -756,7 +784,7 @@ def run_workload(args, log):
                 "algorithmic_bytes_per_launch": alg, "launch_ms": round(kern_ms, 4),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 
-    if args.workload == "gist1m":
+    if name == "gist1m":
         k_dev = torch.from_numpy(kq).cuda()
         ef_dev = torch.from_numpy(efq).cuda()
         ef_max = int(efq.max())
@@ -805,9 +833,8 @@ def run_workload(args, log):
             "clocks": clk.summary(),
             "gpu_launches": args.steps * _launches_per_call(ef_max),
         }
-        print(json.dumps(line), flush=True)
         idx.close()
-        return
+        return line
 
     # unit10m / sift1m_e: calibrate ef for recall@10 >= 0.95 in every p bin,
     # then time the batched form (and, for unit10m, replay Poisson arrivals
@@ -838,7 +865,7 @@ def run_workload(args, log):
                           stats=True, cutoff=w.cutoff)
     st = st.cpu().numpy().astype(np.int64)
     hits_k = _recall_at_k(ids, gt, kq)
-    if args.workload == "sift1m_e":
+    if name == "sift1m_e":
         hk = _recall_at_k(ids, gt, kq)
         value = aggregate_value(args.steps * w.nq, 1, sum(ms) / 1e3)
         line = {
@@ -865,9 +892,8 @@ def run_workload(args, log):
             "clocks": clk.summary(),
             "gpu_launches": args.steps * _launches_per_call(int(efk.max())),
         }
-        print(json.dumps(line), flush=True)
         idx.close()
-        return
+        return line
     serving = []
     for rate in (5_000, 50_000, 100_000, 200_000):
         arr = np.cumsum(np.random.default_rng(7).exponential(1e6 / rate, size=w.nq))
@@ -914,8 +940,8 @@ def run_workload(args, log):
         "gpu_launches": args.steps * _launches_per_call(int(efk.max())),
         "serving": serving,
     }
-    print(json.dumps(line), flush=True)
     idx.close()
+    return line
 
 
 # ---------------------------------------------------------------- t / tau knob
@@ -1063,12 +1089,71 @@ def run_fixed_p(args, log):
 
 
 # ---------------------------------------------------------------- verification
-def run_verify(args, log):
+def verify_roofline(idx, q_dev, w, steps, warmup, t=256, K=50, pv=0.7, n_rows=None):
     """The L_p verification kernel alone (Algorithm 1, lines 6-10, exact mode
-    with the partial-sum drop) on the sift1m recipe: each query's candidate
-    set is its exact L1 top-256 (what candidate generation approximates),
-    p = 0.7 for every query (two SFU operations per term), K = 50.  Reports
-    the SFU operations per second against the nominal SFU rate."""
+    with the partial-sum drop): each query's candidate set is its exact L1
+    top-t (what candidate generation approximates), p = pv for every query
+    (two SFU operations per term).  Two roofs bound the launch: the SFU
+    (2 operations per term the kernel accumulated, by its own counter,
+    against the SFU rate measured right before with uhnsw_probe_sfu) and HBM
+    (the FP32 rows of the candidates, 4 d bytes each, plus the query rows, ids
+    and outputs, against MEASURED_PEAKS.json hbm_gbs).  The binding roof is
+    the one that needs more time; its fraction is the record's frac.  Time:
+    CUDA events around the launch, L2 flushed before each."""
+    import torch
+    from paper_2605_02030_gb300 import uhnsw as U
+
+    nq = q_dev.shape[0]
+    cand = idx.exact(q_dev, torch.ones(nq, device="cuda"), t)[0].to(torch.int32).contiguous()
+    p_dev = torch.full((nq,), pv, dtype=torch.float32, device="cuda")
+    flush = torch.empty(384 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ms = []
+    for i in range(warmup + steps):
+        flush.fill_(1.0)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        idx.verify(q_dev, p_dev, cand, K)
+        e.record()
+        torch.cuda.synchronize()
+        if i >= warmup:
+            ms.append(a.elapsed_time(e))
+    _, _, st = idx.verify(q_dev, p_dev, cand, K, stats=True)
+    st = st.cpu().numpy().astype(np.int64)
+    terms = int(st[:, 2].sum())
+    started = int(st[:, 1].sum())
+    mean_s = statistics.mean(ms) / 1e3
+    sfu_ops = 2 * terms
+    sfu_peak = max(o / (m / 1e3) for m, o in (U.probe_sfu(16, 4096) for _ in range(3)))
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0) * 1e9
+    alg_bytes = started * w.d * 4 + nq * (w.d * 4 + 4 + t * 4 + K * 12)
+    t_sfu, t_hbm = sfu_ops / sfu_peak, alg_bytes / hbm_peak
+    sfu = {"achieved": round(sfu_ops / mean_s / 1e12, 4), "peak": round(sfu_peak / 1e12, 4),
+           "unit": "T SFU ops/s", "frac": round(sfu_ops / mean_s / sfu_peak, 4),
+           "peak_source": "uhnsw_probe_sfu on this device (lg2 + ex2 chains, best of 3), "
+                          "of measured"}
+    hbm = {"achieved": round(alg_bytes / mean_s / 1e9, 1), "peak": round(hbm_peak / 1e9, 1),
+           "unit": "GB/s", "frac": round(alg_bytes / mean_s / hbm_peak, 4),
+           "algorithmic_bytes_per_launch": alg_bytes,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    bound = "alu" if t_sfu >= t_hbm else "hbm"
+    top = sfu if bound == "alu" else hbm
+    return {"bound": bound, "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
+            "frac": top["frac"], "kernel": "uhnsw_wverify_kernel (warp per query)",
+            "launch_ms": round(mean_s * 1e3, 4), "sfu": sfu, "hbm": hbm,
+            "workload": f"{nq:,} queries of {w.name} on the first {n_rows or w.n:,} rows, "
+                        f"candidates = exact L1 top-{t}, p = {pv}, K = {K}",
+            "terms_per_query": round(terms / nq, 1),
+            "terms_without_drop_per_query": t * w.d}
+
+
+def run_verify(args, log):
+    """The L_p verification kernel alone on the sift1m recipe, against the
+    SFU rate measured on the device (see verify_roofline)."""
     import torch
     import paper_2605_02030_gb300 as pkg
     from paper_2605_02030_gb300 import uhnsw as U
@@ -1078,43 +1163,58 @@ def run_verify(args, log):
     base = I.base_vectors(w)
     qs = I.query_vectors(w)
     g1, g2 = graphs_for(w, base, log)
-    idx = U.Index(base, g1, g2)
     q_dev = torch.from_numpy(qs).cuda()
-    t, K = 256, 50
-    cand = idx.exact(q_dev, torch.ones(w.nq, device="cuda"), t)[0].to(torch.int32).contiguous()
-    p_dev = torch.full((w.nq,), 0.7, dtype=torch.float32, device="cuda")
+    records = {}
+    # the full 1M-row base (rows come from HBM: 0.5 SFU operation per byte,
+    # below the ~1 op/B at which the SFU and HBM roofs meet), and its first
+    # 100,000 rows (51 MB, L2-resident: the SFU roof binds)
+    for n_rows in (w.n, min(w.n, 100_000)):
+        sub = np.ascontiguousarray(base[:n_rows])
+        # (the verification reads no graph; a subset index still needs one)
+        gs = ((g1, g2) if n_rows == w.n else
+              (None, U.build_graph(sub, 2, 8, 32, I.hnsw_levels(n_rows, 8, 99), threads=0)))
+        idx = U.Index(sub, *gs)
+        records[str(n_rows)] = verify_roofline(idx, q_dev, w, args.steps, args.warmup,
+                                               n_rows=n_rows)
+        idx.close()
+    line = {"metric": "L_p verification alone (p = 0.7, t = 256, K = 50): fraction of the "
+                      "binding roof (SFU or HBM)", "records": records}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- profiling run
+def run_profile(args, log):
+    """A short fixed run for profiler captures: the FP16 batched form on the
+    headline workload at --ef (default 48) and the first of --widths, three
+    warm-up launches and --steps launches of the search, L2 flushed before
+    each.  No calibration, so the launch order is fixed: the search kernel's
+    launches are the warm-ups, then the steps."""
+    import torch
+    import paper_2605_02030_gb300 as pkg
+    from paper_2605_02030_gb300 import uhnsw as U
+
+    pkg.build()
+    w = workload(args)
+    base = I.base_vectors(w)
+    qs = I.query_vectors(w)
+    p = I.query_params(w)[0]
+    g1, g2 = graphs_for(w, base, log)
+    idx = U.Index(base, g1, g2, traverse_dtype="f16")
+    q, pd = torch.from_numpy(qs).cuda(), torch.from_numpy(p).cuda()
+    ef, width = args.ef or 48, int(args.widths.split(",")[0])
     flush = torch.empty(384 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ms = []
-    for i in range(args.warmup + args.steps):
+    for i in range(3 + args.steps):
         flush.fill_(1.0)
-        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        idx.verify(q_dev, p_dev, cand, K)
-        e.record()
+        idx.search(q, pd, k=10, ef=ef, width=width, persistent=True)
+        b.record()
         torch.cuda.synchronize()
-        if i >= args.warmup:
-            ms.append(a.elapsed_time(e))
-    _, _, st = idx.verify(q_dev, p_dev, cand, K, stats=True)
-    st = st.cpu().numpy().astype(np.int64)
-    terms = int(st[:, 2].sum())
-    mean_ms = statistics.mean(ms)
-    sfu_ops = 2 * terms                      # lg2 and ex2 per term
-    # nominal SFU rate: 16 lg2 / ex2 results per SM per clock
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    peak = sms * 16 * 2.07e9
-    line = {"metric": "L_p verification alone: SFU operations per second (p = 0.7, t = 256, K = 50)",
-            "value": round(sfu_ops / (mean_ms / 1e3) / 1e12, 4), "unit": "T SFU ops/s",
-            "ms_per_launch": round(mean_ms, 4),
-            "roofline": {"bound": "alu", "achieved": round(sfu_ops / (mean_ms / 1e3) / 1e12, 4),
-                         "peak": round(peak / 1e12, 3), "unit": "T SFU ops/s",
-                         "frac": round(sfu_ops / (mean_ms / 1e3) / peak, 4),
-                         "peak_source": f"nominal: {sms} SMs x 16 lg2/ex2 per clock x 2.07 GHz"},
-            "config": {"workload": f"sift1m: N={w.n:,} d={w.d}, {w.nq:,} queries, candidates = "
-                                   "exact L1 top-256 of each query",
-                       "terms_per_query": round(terms / w.nq, 1),
-                       "terms_without_drop_per_query": t * w.d,
-                       "candidates_started_per_query": float(st[:, 1].mean())}}
-    print(json.dumps(line), flush=True)
+        if i >= 3:
+            ms.append(a.elapsed_time(b))
+    print(json.dumps({"profile_run": f"{w.name} ef={ef} width={width}",
+                      "ms_median": round(statistics.median(ms), 4)}), flush=True)
     idx.close()
 
 
@@ -1271,8 +1371,12 @@ def main():
     ap.add_argument("--nq", type=int, default=0, help="queries per step override")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the full-size records of the other workloads in the default run")
+    ap.add_argument("--extras", default="gist1m,unit10m",
+                    help="workloads recorded after the headline (comma-separated)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-ef", type=int, default=48,
+    ap.add_argument("--ref-ef", type=int, default=52,
                     help="beam of the oracle arm (the GPU's calibrated operating point)")
     ap.add_argument("--ref-queries-per-step", type=int, default=64,
                     help="oracle-arm queries per step and host core")
@@ -1301,6 +1405,8 @@ def main():
                     help="comma-separated p of the --fixed-p sweep")
     ap.add_argument("--verify-roofline", action="store_true",
                     help="the L_p verification kernel alone, against the SFU rate")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="a short fixed run of the FP16 batched search for profiler captures")
     ap.add_argument("--probes", action="store_true",
                     help="measure the SFU rate and the L2 / HBM row-gather bandwidth")
     ap.add_argument("--quiet", action="store_true")
@@ -1321,6 +1427,8 @@ def main():
         run_verify(args, log)
     elif args.probes:
         run_probes(args, log)
+    elif args.profile_run:
+        run_profile(args, log)
     elif args.workload != "sift1m":
         run_workload(args, log)
     else:

@@ -36,6 +36,8 @@ dataset item is reproduced):
                centre mu ~ Beta(2, 5) per dimension, x ~ Beta(20 mu,
                20 (1 - mu)); p ~ U(0.5, 2]; k in {1, 10, 100}; ef in
                {32, 64, 128, 256, 512} with ef >= k; BF16 traversal copy.
+               Its rows are drawn in blocks of 16,384, block i from child i
+               of a seed drawn from the workload's stream.
   unit10m      N=10,000,000 d=96 N(0, I) rows scaled to unit L2 norm, FP16;
                p ~ U(0.5, 2]; k in {10, 50}.
   sift1m_e     sift1m's base and queries for U-HNSW-E (Section 4.5): graphs
@@ -45,6 +47,8 @@ dataset item is reproduced):
 from __future__ import annotations
 
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field, replace
 
 import numpy as np
@@ -136,13 +140,24 @@ def _draw_points(w: Workload, rng: np.random.Generator, n: int, centres) -> np.n
             v = centres[c] + rng.standard_normal((m, w.d), dtype=np.float32) * 20.0
             x[s:s + m] = np.rint(np.clip(v, 0.0, 255.0))
     elif w.kind == "gist":
+        # Beta draws are slow: each block of 16,384 rows has a stream of its
+        # own (child i of the stream's seed), so the blocks are drawn on
+        # several threads and the array does not depend on their number
         x = np.empty((n, w.d), dtype=np.float32)
         step = 16384
-        for s in range(0, n, step):
+        seed = int(rng.integers(0, 2 ** 63))
+
+        def block(i):
+            s = i * step
             m = min(step, n - s)
-            c = rng.integers(0, centres.shape[0], size=m)
+            r = np.random.default_rng(np.random.SeedSequence(seed, spawn_key=(i,)))
+            c = r.integers(0, centres.shape[0], size=m)
             mu = np.clip(centres[c], 1e-3, 1 - 1e-3)
-            x[s:s + m] = rng.beta(20.0 * mu, 20.0 * (1.0 - mu)).astype(np.float32)
+            x[s:s + m] = r.beta(20.0 * mu, 20.0 * (1.0 - mu)).astype(np.float32)
+
+        nblocks = (n + step - 1) // step
+        with ThreadPoolExecutor(max_workers=max(1, min(nblocks, os.cpu_count() or 1))) as ex:
+            list(ex.map(block, range(nblocks)))
     elif w.kind == "unit":
         x = np.empty((n, w.d), dtype=np.float32)
         step = 1 << 18
