@@ -822,6 +822,9 @@ def workload_record(args, log, name, sized=False):
                        "autotuned": tuned,
                        "l2": "flushed (384 MB write) between timed steps",
                        "recall_at_k": round(float(hits.mean()), 4),
+                       "recall_note": "at the configuration's own per-query ef, drawn from "
+                                      "{32, 64, 128, 256, 512} with ef >= k (no beam is "
+                                      "calibrated for this workload)",
                        "recall_at_k_by_k": {int(kk): round(float(hits[kg == kk].mean()), 4)
                                             for kk in np.unique(kg)},
                        "recall_at_k_min_p_bin": round(min(float(hits[bins == b].mean())
@@ -841,12 +844,15 @@ def workload_record(args, log, name, sized=False):
     # through the serving loop)
     k10 = np.full(w.nq, 10, np.int32)
     ef_op = None
+    curve = []
     for ef in EF_SWEEP:
         ids, _, _ = idx.search(q_dev, p_dev, k=10, ef=ef, persistent=True, cutoff=w.cutoff)
         torch.cuda.synchronize()
         hits = _recall_at_k(ids.cpu().numpy(), gt, k10[:ng])
         per = [float(hits[bins == b].mean()) for b in np.unique(bins)]
         ef_op, rec10, rec10_min = ef, float(hits.mean()), min(per)
+        curve.append({"ef": ef, "recall_at_10": round(rec10, 4),
+                      "recall_at_10_min_p_bin": round(rec10_min, 4)})
         if rec10_min >= RECALL_TARGET:
             break
     log(f"operating point ef={ef_op}: recall@10 {rec10:.4f}, worst p bin {rec10_min:.4f}")
@@ -881,6 +887,8 @@ def workload_record(args, log, name, sized=False):
                                "CUDA-graph replay",
                        "ef": ef_op, "recall_at_10": round(rec10, 4),
                        "recall_at_10_min_p_bin": round(rec10_min, 4),
+                       "recall_target_met": bool(rec10_min >= RECALL_TARGET),
+                       "recall_curve": curve,
                        "recall_at_10_per_p_bin": {
                            bin_label(w, b): round(float(hk[bins == b].mean()), 4)
                            for b in np.unique(bins)},
@@ -930,6 +938,11 @@ def workload_record(args, log, name, sized=False):
                            "arrivals through the continuous-batching server",
                    "ef": ef_op, "recall_at_10": round(rec10, 4),
                    "recall_at_10_min_p_bin": round(rec10_min, 4),
+                   "recall_target_met": bool(rec10_min >= RECALL_TARGET),
+                   "recall_note": "the smallest beam up to the cap of 512 whose worst p bin "
+                                  "reaches 0.95, else the cap; this isotropic recipe stays far "
+                                  "below the target there (recall_curve)",
+                   "recall_curve": curve,
                    "recall_at_k": round(float(hits_k.mean()), 4),
                    "dist_rel_err_vs_fp64_max": _dist_rel_err(base, qs, p, ids, dist, sample),
                    "l2": "flushed (384 MB write) between timed steps",
