@@ -474,8 +474,8 @@ def run_ours(args, log):
     # the verification kernel alone against the SFU rate measured on this device
     vroof = verify_roofline(idx32 if idx32 is not None else idx16, q_dev, w,
                             max(5, args.steps // 2), args.warmup)
-    log(f"verification alone: {vroof['achieved']} of {vroof['peak']} T SFU ops/s "
-        f"({vroof['frac']})")
+    log(f"verification alone: {vroof['achieved']} of {vroof['peak']} {vroof['unit']} "
+        f"({vroof['frac']}, bound {vroof['bound']})")
 
     # end to end through the public C ABI with host buffers (copies inside the timed region)
     pin_q = torch.from_numpy(qs).pin_memory().numpy()
