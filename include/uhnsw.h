@@ -142,8 +142,11 @@ typedef struct {
                             queue is ordered by graph and p form, so that the queries in
                             flight on an SM run the same code.  With per-query ef it is
                             also bucketed by beam (<= 64, 128, 256, 512), one launch per
-                            bucket sized for its beam.  Persistent searches on one index
-                            must not overlap on the GPU (the server never uses them). */
+                            bucket sized for its beam.  Each stream has a queue of its
+                            own (created on its first persistent search), so persistent
+                            searches on different streams may overlap on the GPU: a
+                            launch's blocks fill the SMs that the previous batch's
+                            finished blocks leave. */
   int32_t use_graph;     /* 1: capture the launch sequence once per call shape, then replay */
   int32_t ef_max;        /* bound on ef' over the batch when per-query ef is given; 0 => 512 */
   int32_t query_threads; /* threads per query: 32 = one warp per query (4 queries per
@@ -233,14 +236,31 @@ int uhnsw_search(uhnsw_index* idx, const float* q, const float* p, const int32_t
  * uhnsw_search with HOST arrays: q (nq x d), p, k, ef (or NULL), the outputs
  * and opts->t_per_query / tau_per_query (if set) are host memory (pinned
  * memory makes the copies asynchronous).  The call
- * copies the inputs to device staging buffers owned by the index, runs the
- * search on `stream` and copies the results back; it returns after the
- * stream has synchronised.  Not safe to run concurrently on one index.
+ * copies the inputs to device staging buffers that the index holds for
+ * `stream`, runs the search on `stream` and copies the results back; it
+ * returns after the stream has synchronised.  opts->use_graph is ignored.
+ * Calls on different streams may run concurrently; calls on one stream from
+ * several threads are serialised by the index.
  */
 int uhnsw_search_host(uhnsw_index* idx, const float* q, const float* p, const int32_t* k,
                       const int32_t* ef, int64_t nq, int32_t k_max, int32_t ef_default,
                       const uhnsw_search_opts* opts, int64_t* out_ids, float* out_dist,
                       void* stream);
+
+/*
+ * uhnsw_search_host without the final wait: returns once the copies in, the
+ * search and the copies out are queued on `stream`.  The host inputs must
+ * stay unchanged and the outputs unread until `stream` has synchronised (an
+ * event recorded after the call marks completion).  With pinned host buffers
+ * the copies run asynchronously, so batches queued on two streams overlap
+ * one batch's copies and search with the other's.  A call whose staging must
+ * grow first waits for the stream's earlier work.  Not capturable in a CUDA
+ * graph.  Errors as uhnsw_search_host.
+ */
+int uhnsw_search_host_async(uhnsw_index* idx, const float* q, const float* p, const int32_t* k,
+                            const int32_t* ef, int64_t nq, int32_t k_max, int32_t ef_default,
+                            const uhnsw_search_opts* opts, int64_t* out_ids, float* out_dist,
+                            void* stream);
 
 /*
  * Candidate verification alone (Algorithm 1 lines 6-10, or the exact mode) on

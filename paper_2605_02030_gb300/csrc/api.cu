@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -67,6 +68,10 @@ int cuda_fail(cudaError_t e, const char* what) {
   return fail(e == cudaErrorMemoryAllocation ? UHNSW_EOOM : UHNSW_ECUDA, "%s: %s", what,
               cudaGetErrorString(e));
 }
+int cuda_fail(cudaError_t e, const char* fn, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? UHNSW_EOOM : UHNSW_ECUDA, "%s: %s: %s", fn, what,
+              cudaGetErrorString(e));
+}
 
 int next_pow2_bits(int64_t x) {
   int b = 0;
@@ -89,20 +94,33 @@ struct uhnsw_index {
   void* trav = nullptr;
   DevGraph g[2];
   int32_t* err = nullptr;         // sticky device error word
-  int32_t* queue_head = nullptr;  // persistent-launch work counter
   int64_t bytes = 0;
   cudaStream_t capture_stream = nullptr;
   std::mutex mu;
   std::vector<GraphEntry> graphs;
-  // host-buffer search staging
-  void* stage = nullptr;
-  size_t stage_bytes = 0;
   // exact-search workspace
   void* exact_ws = nullptr;
   size_t exact_ws_bytes = 0;
-  // persistent-search queue order: bin counters and cursors, bucket slots, the order array
-  int32_t* bucket_ws = nullptr;
-  int64_t bucket_cap = 0;
+  // State of each stream that searched this index, so that searches on
+  // different streams may overlap on the GPU.  The persistent-search queue:
+  // work counters (one per beam bucket) and the ordering workspace (bin
+  // counters and cursors, bucket slots, the order array); a workspace that
+  // grows keeps its old buffer alive until the index is freed, since CUDA
+  // graphs captured on that stream still point at it.  The host-buffer
+  // searches' device staging, with a lock that keeps one call's copies,
+  // search and copies back together on the stream.
+  struct StreamState {
+    void* stream = nullptr;
+    int32_t* head = nullptr;
+    int32_t* ws = nullptr;
+    int64_t cap = 0;
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    std::mutex host_mu;
+  };
+  std::vector<std::unique_ptr<StreamState>> streams;
+  std::vector<void*> retired;
+  std::mutex streams_mu;
   // autotuned launch configurations: key (ef bucket, k bucket) -> options
   std::vector<std::pair<int64_t, uhnsw_search_opts>> tuned;
   std::mutex tuned_mu;
@@ -117,10 +135,13 @@ struct uhnsw_index {
     if (trav && trav != base32) cudaFree(trav);
     cudaFree(base32);
     cudaFree(err);
-    cudaFree(queue_head);
-    cudaFree(stage);
+    for (auto& ss : streams) {
+      cudaFree(ss->head);
+      cudaFree(ss->ws);
+      cudaFree(ss->stage);
+    }
+    for (void* r : retired) cudaFree(r);
     cudaFree(exact_ws);
-    cudaFree(bucket_ws);
     if (capture_stream) cudaStreamDestroy(capture_stream);
   }
 };
@@ -350,7 +371,6 @@ extern "C" int uhnsw_load(const float* base, int64_t n, int32_t d, const uhnsw_g
     }
     if (rc != UHNSW_OK) break;
     e = cudaMalloc(&idx->err, 16);
-    if (e == cudaSuccess) e = cudaMalloc(&idx->queue_head, 64);
     if (e == cudaSuccess) e = cudaMemset(idx->err, 0, 16);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&idx->capture_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) { rc = cuda_fail(e, "uhnsw_load: state"); break; }
@@ -383,6 +403,8 @@ struct Prepared {
   bool bucketed = false;
   BeamBuckets bb;
   cudaEvent_t events[2] = {nullptr, nullptr};  // opts.kernel_events, if given
+  int32_t* qhead = nullptr;  // the stream's queue (persistent search)
+  int32_t* qws = nullptr;
   std::vector<Launch> launches;
 };
 
@@ -396,10 +418,52 @@ int visited_bits(int asked, int bound, int width, int deg0) {
   return std::max(asked, next_pow2_bits(2ll * (bound + width * deg0)));
 }
 
-// Validates host-side search arguments and fills the launch description.
+// The state of `stream` (created on the stream's first search that needs it).
+int stream_state(uhnsw_index* idx, void* stream, uhnsw_index::StreamState** out) {
+  std::lock_guard<std::mutex> lock(idx->streams_mu);
+  for (auto& x : idx->streams)
+    if (x->stream == stream) {
+      *out = x.get();
+      return UHNSW_OK;
+    }
+  std::unique_ptr<uhnsw_index::StreamState> fresh(new (std::nothrow) uhnsw_index::StreamState);
+  if (!fresh) return fail(UHNSW_EOOM, "uhnsw_search: stream state");
+  fresh->stream = stream;
+  *out = fresh.get();
+  idx->streams.push_back(std::move(fresh));
+  return UHNSW_OK;
+}
+
+// The persistent-search queue of `stream` with an ordering workspace of at
+// least `need` words.
+int queue_for(uhnsw_index* idx, void* stream, int64_t need, uhnsw_index::StreamState** out) {
+  uhnsw_index::StreamState* qu = nullptr;
+  int rc = stream_state(idx, stream, &qu);
+  if (rc != UHNSW_OK) return rc;
+  std::lock_guard<std::mutex> lock(idx->streams_mu);
+  if (!qu->head) {
+    cudaError_t e = cudaMalloc(&qu->head, 16 * sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: queue counters");
+  }
+  if (need > qu->cap) {
+    const int64_t cap = std::max(need, 2 * qu->cap);
+    int32_t* ws = nullptr;
+    cudaError_t e = cudaMalloc(&ws, cap * sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: queue workspace");
+    if (qu->ws) idx->retired.push_back(qu->ws);
+    qu->ws = ws;
+    qu->cap = cap;
+  }
+  *out = qu;
+  return UHNSW_OK;
+}
+
+// Validates host-side search arguments and fills the launch description for
+// a search queued on `stream`.
 int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32_t* k,
                    const int32_t* ef, int64_t nq, int32_t k_max, int32_t ef_default,
-                   const uhnsw_search_opts* o, int64_t* out_ids, float* out_dist, Prepared* P) {
+                   const uhnsw_search_opts* o, int64_t* out_ids, float* out_dist, void* stream,
+                   Prepared* P) {
   if (!idx) return fail(UHNSW_EINVAL, "uhnsw_search: index is NULL");
   if (nq < 0 || nq > INT32_MAX) return fail(UHNSW_EINVAL, "uhnsw_search: nq=%lld", (long long)nq);
   if (nq > 0 && (!q || !p || !out_ids || !out_dist))
@@ -520,7 +584,7 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   a.stats = opts.stats;
   a.err = idx->err;
   a.trav_exact = idx->trav_exact ? 1 : 0;
-  a.queue_head = opts.persistent ? idx->queue_head : nullptr;
+  a.queue_head = nullptr;  // set below for a persistent search
   a.sb = 0;
   P->shape = sh;
   P->wshape = wsh;
@@ -576,22 +640,18 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
       for (int bound : {64, 128, 256, 512})
         if (bound < ef_cap) P->bb.bound[P->bb.n++] = bound;
     P->bb.bound[P->bb.n++] = ef_cap;
-    const int64_t need = kBucketOrder + nq;
-    if (need > idx->bucket_cap) {
-      cudaFree(idx->bucket_ws);
-      idx->bucket_ws = nullptr;
-      idx->bucket_cap = 0;
-      cudaError_t e = cudaMalloc(&idx->bucket_ws, need * sizeof(int32_t));
-      if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: bucket scratch");
-      idx->bucket_cap = need;
-    }
+    uhnsw_index::StreamState* qu = nullptr;
+    const int rq = queue_for(idx, stream, kBucketOrder + nq, &qu);
+    if (rq != UHNSW_OK) return rq;
+    P->qhead = qu->head;
+    P->qws = qu->ws;
     for (int b = P->bb.n - 1; b >= 0; --b) {
       Launch Lb;
       const int rc = describe(P->bb.bound[b], &Lb);
       if (rc != UHNSW_OK) return rc;
-      Lb.a.queue_head = idx->queue_head + b;
-      Lb.a.qorder = idx->bucket_ws + kBucketOrder;
-      Lb.a.qbucket = idx->bucket_ws + kBucketInfo + 2 * b;
+      Lb.a.queue_head = qu->head + b;
+      Lb.a.qorder = qu->ws + kBucketOrder;
+      Lb.a.qbucket = qu->ws + kBucketInfo + 2 * b;
       P->launches.push_back(Lb);
     }
   } else {
@@ -607,13 +667,10 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
 int enqueue_search(uhnsw_index* idx, const Prepared& P, cudaStream_t st) {
   if (P.a.nq == 0) return UHNSW_OK;
   cudaError_t e;
-  if (P.persistent) {
-    e = cudaMemsetAsync(idx->queue_head, 0, 16 * sizeof(int32_t), st);
-    if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: queue reset");
-  }
   if (P.bucketed) {
-    e = launch_bucketing(P.a, P.bb, idx->bucket_ws, idx->bucket_ws + kBucketOrder,
-                         idx->bucket_ws + kBucketInfo, st);
+    e = cudaMemsetAsync(P.qhead, 0, 16 * sizeof(int32_t), st);
+    if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: queue reset");
+    e = launch_bucketing(P.a, P.bb, P.qws, P.qws + kBucketOrder, P.qws + kBucketInfo, st);
     if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search: bucketing");
   }
   if (P.events[0]) {
@@ -640,7 +697,8 @@ extern "C" int uhnsw_search(uhnsw_index* idx, const float* q, const float* p, co
                             void* stream) {
   clear_error();
   Prepared P;
-  int rc = prepare_search(idx, q, p, k, ef, nq, k_max, ef_default, opts, out_ids, out_dist, &P);
+  int rc = prepare_search(idx, q, p, k, ef, nq, k_max, ef_default, opts, out_ids, out_dist, stream,
+                          &P);
   if (rc != UHNSW_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   // A plain cudaEventRecord inside a stream capture only marks a dependency
@@ -693,16 +751,21 @@ extern "C" int uhnsw_search(uhnsw_index* idx, const float* q, const float* p, co
   return e == cudaSuccess ? UHNSW_OK : cuda_fail(e, "uhnsw_search: cudaGraphLaunch");
 }
 
-extern "C" int uhnsw_search_host(uhnsw_index* idx, const float* q, const float* p, const int32_t* k,
-                                 const int32_t* ef, int64_t nq, int32_t k_max, int32_t ef_default,
-                                 const uhnsw_search_opts* opts, int64_t* out_ids, float* out_dist,
-                                 void* stream) {
+namespace {
+
+// uhnsw_search_host and uhnsw_search_host_async: the inputs copied into the
+// stream's staging, the search, the results copied back, all queued on
+// `stream`; `wait` then synchronises the stream.
+int search_host_impl(const char* fn, uhnsw_index* idx, const float* q, const float* p,
+                     const int32_t* k, const int32_t* ef, int64_t nq, int32_t k_max,
+                     int32_t ef_default, const uhnsw_search_opts* opts, int64_t* out_ids,
+                     float* out_dist, void* stream, bool wait) {
   clear_error();
-  if (!idx) return fail(UHNSW_EINVAL, "uhnsw_search_host: index is NULL");
-  if (nq < 0 || nq > INT32_MAX) return fail(UHNSW_EINVAL, "uhnsw_search_host: nq");
+  if (!idx) return fail(UHNSW_EINVAL, "%s: index is NULL", fn);
+  if (nq < 0 || nq > INT32_MAX) return fail(UHNSW_EINVAL, "%s: nq", fn);
   if (nq == 0) return UHNSW_OK;
-  if (!q || !p || !out_ids || !out_dist) return fail(UHNSW_EINVAL, "uhnsw_search_host: NULL pointer");
-  if (k_max < 1 || k_max > UHNSW_MAX_EF) return fail(UHNSW_EINVAL, "uhnsw_search_host: k_max");
+  if (!q || !p || !out_ids || !out_dist) return fail(UHNSW_EINVAL, "%s: NULL pointer", fn);
+  if (k_max < 1 || k_max > UHNSW_MAX_EF) return fail(UHNSW_EINVAL, "%s: k_max", fn);
   const int32_t* ht = opts ? opts->t_per_query : nullptr;    // host arrays here
   const float* htau = opts ? opts->tau_per_query : nullptr;
   const size_t bq = (size_t)nq * idx->d * 4, bp = (size_t)nq * 4, bk = k ? (size_t)nq * 4 : 0,
@@ -711,16 +774,22 @@ extern "C" int uhnsw_search_host(uhnsw_index* idx, const float* q, const float* 
                bta = htau ? (size_t)nq * 4 : 0;
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
   const size_t need = al(bq) + al(bp) + al(bk) + al(be) + al(bi) + al(bd) + al(bt) + al(bta);
-  std::lock_guard<std::mutex> lock(idx->mu);
-  if (need > idx->stage_bytes) {
-    cudaFree(idx->stage);
-    idx->stage = nullptr;
-    idx->stage_bytes = 0;
-    cudaError_t e = cudaMalloc(&idx->stage, need);
-    if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search_host: staging");
-    idx->stage_bytes = need;
+  uhnsw_index::StreamState* ss = nullptr;
+  int rc = stream_state(idx, stream, &ss);
+  if (rc != UHNSW_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lock(ss->host_mu);
+  if (need > ss->stage_bytes) {
+    // the stream's earlier searches may still read the old staging
+    cudaError_t e = ss->stage ? cudaStreamSynchronize(st) : cudaSuccess;
+    if (e == cudaSuccess) e = cudaFree(ss->stage);
+    ss->stage = nullptr;
+    ss->stage_bytes = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&ss->stage, need);
+    if (e != cudaSuccess) return cuda_fail(e, fn, "staging");
+    ss->stage_bytes = need;
   }
-  char* s = (char*)idx->stage;
+  char* s = (char*)ss->stage;
   float* dq = (float*)s; s += al(bq);
   float* dp = (float*)s; s += al(bp);
   int32_t* dk = k ? (int32_t*)s : nullptr; s += al(bk);
@@ -736,23 +805,41 @@ extern "C" int uhnsw_search_host(uhnsw_index* idx, const float* q, const float* 
   o2.use_graph = 0;
   o2.t_per_query = dt;
   o2.tau_per_query = dta;
-  int rc = prepare_search(idx, dq, dp, dk, de, nq, k_max, ef_default, &o2, di, dd, &P);
+  rc = prepare_search(idx, dq, dp, dk, de, nq, k_max, ef_default, &o2, di, dd, stream, &P);
   if (rc != UHNSW_OK) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(dq, q, bq, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dp, p, bp, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && k) e = cudaMemcpyAsync(dk, k, bk, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && ef) e = cudaMemcpyAsync(de, ef, be, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && ht) e = cudaMemcpyAsync(dt, ht, bt, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && htau) e = cudaMemcpyAsync(dta, htau, bta, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search_host: upload");
+  if (e != cudaSuccess) return cuda_fail(e, fn, "upload");
   rc = enqueue_search(idx, P, st);
   if (rc != UHNSW_OK) return rc;
   e = cudaMemcpyAsync(out_ids, di, bi, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out_dist, dd, bd, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(e, "uhnsw_search_host: download");
+  if (e == cudaSuccess && wait) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, fn, "download");
   return UHNSW_OK;
+}
+
+}  // namespace
+
+extern "C" int uhnsw_search_host(uhnsw_index* idx, const float* q, const float* p, const int32_t* k,
+                                 const int32_t* ef, int64_t nq, int32_t k_max, int32_t ef_default,
+                                 const uhnsw_search_opts* opts, int64_t* out_ids, float* out_dist,
+                                 void* stream) {
+  return search_host_impl("uhnsw_search_host", idx, q, p, k, ef, nq, k_max, ef_default, opts,
+                          out_ids, out_dist, stream, true);
+}
+
+extern "C" int uhnsw_search_host_async(uhnsw_index* idx, const float* q, const float* p,
+                                       const int32_t* k, const int32_t* ef, int64_t nq,
+                                       int32_t k_max, int32_t ef_default,
+                                       const uhnsw_search_opts* opts, int64_t* out_ids,
+                                       float* out_dist, void* stream) {
+  return search_host_impl("uhnsw_search_host_async", idx, q, p, k, ef, nq, k_max, ef_default,
+                          opts, out_ids, out_dist, stream, false);
 }
 
 extern "C" int uhnsw_verify(uhnsw_index* idx, const float* q, const float* p, const int32_t* cand,

@@ -143,7 +143,6 @@ int launch_batch(uhnsw_server* s, Lane& L, int device) {
   uhnsw_search_opts so = s->o.search;
   so.stats = nullptr;
   so.use_graph = 0;
-  so.persistent = 0;  // the index's queue counter serves one persistent search at a time
   so.kernel_events = nullptr;
   so.t_per_query = nullptr;  // per-request t / tau are not part of a server request
   so.tau_per_query = nullptr;

@@ -78,7 +78,7 @@ class _SearchOpts(C.Structure):
     ]
 
 
-EXPORTS = ("uhnsw_load", "uhnsw_search", "uhnsw_search_host", "uhnsw_verify", "uhnsw_exact",
+EXPORTS = ("uhnsw_load", "uhnsw_search", "uhnsw_search_host", "uhnsw_search_host_async", "uhnsw_verify", "uhnsw_exact",
            "uhnsw_idealized_recall", "uhnsw_plan_t",
            "uhnsw_exact_static", "uhnsw_server_create", "uhnsw_server_submit", "uhnsw_server_poll",
            "uhnsw_server_wait", "uhnsw_server_replay", "uhnsw_server_stats",
@@ -110,6 +110,8 @@ def load_library():
     lib.uhnsw_search.argtypes = [P, P, P, P, P, I64, I32, I32, P, P, P, P]
     lib.uhnsw_search_host.restype = C.c_int
     lib.uhnsw_search_host.argtypes = [P, P, P, P, P, I64, I32, I32, P, P, P, P]
+    lib.uhnsw_search_host_async.restype = C.c_int
+    lib.uhnsw_search_host_async.argtypes = [P, P, P, P, P, I64, I32, I32, P, P, P, P]
     lib.uhnsw_verify.restype = C.c_int
     lib.uhnsw_verify.argtypes = [P, P, P, P, I32, I32, I64, P, P, P, P]
     lib.uhnsw_exact.restype = C.c_int
@@ -393,9 +395,15 @@ class Index:
         return ids, dist, st
 
     def search_host(self, q: np.ndarray, p: np.ndarray, k=10, ef=64, *, k_max: int | None = None,
-                    out=None, stream=None, **kw):
-        """uhnsw_search_host: host (pinned or pageable) arrays in and out."""
+                    out=None, stream=None, wait: bool = True, **kw):
+        """uhnsw_search_host: host (pinned or pageable) arrays in and out.
+        wait=False calls uhnsw_search_host_async, which returns once the work
+        is queued on `stream`: then `out` must be given, every array must
+        already be C-contiguous float32 / int32 (the call makes no temporary
+        copies that could be freed before the stream reads them), and none
+        may be touched until the stream has synchronised."""
         lib = load_library()
+        given = [q, p] + [x for x in (k, ef, kw.get("t"), kw.get("tau")) if isinstance(x, np.ndarray)]
         q = np.ascontiguousarray(q, np.float32)
         p = np.ascontiguousarray(p, np.float32)
         nq = q.shape[0]
@@ -404,13 +412,23 @@ class Index:
         if k_max is None:
             k_max = int(k_a.max()) if k_a is not None else int(k)
         elif k_a is None and int(k) != k_max:
+            if not wait:
+                raise ValueError("search_host(wait=False): pass k as an int32 array or k == k_max")
             k_a = np.full(nq, int(k), np.int32)
+        if not wait:
+            if out is None:
+                raise ValueError("search_host(wait=False): `out` must be given")
+            used = [q, p] + [x for x in (k_a, ef_a) if x is not None]
+            if any(u is not g for u, g in zip(used, given)):
+                raise ValueError("search_host(wait=False): arrays must be C-contiguous float32 "
+                                 "(q, p) / int32 (k, ef) already")
         ef_default = int(ef) if ef_a is None else max(1, int(kw.get("ef_max", 0)) or MAX_EF)
         if out is None:
             ids = np.empty((nq, k_max), np.int64)
             dist = np.empty((nq, k_max), np.float32)
         else:
             ids, dist = out
+        t_in, tau_in = kw.get("t"), kw.get("tau")
         t_a = (np.ascontiguousarray(kw.pop("t"), np.int32)
                if isinstance(kw.get("t"), np.ndarray) else None)
         tau_a = (np.ascontiguousarray(kw.pop("tau"), np.float32)
@@ -419,11 +437,15 @@ class Index:
                                              "persistent", "ef_max", "query_threads",
                                              "stage_bytes", "team_lanes", "hash_bits",
                                              "verify_groups") if x in kw})
+        if not wait and any(a is not None and a is not kw_in for a, kw_in in
+                            ((t_a, t_in), (tau_a, tau_in))):
+            raise ValueError("search_host(wait=False): t / tau arrays must be C-contiguous "
+                             "int32 / float32 already")
         o.t_per_query = t_a.ctypes.data if t_a is not None else None
         o.tau_per_query = tau_a.ctypes.data if tau_a is not None else None
-        _check(lib.uhnsw_search_host(self._h, _np_ptr(q), _np_ptr(p), _np_ptr(k_a), _np_ptr(ef_a),
-                                     nq, k_max, ef_default, C.byref(o), _np_ptr(ids),
-                                     _np_ptr(dist), _stream_ptr(stream)))
+        fn = lib.uhnsw_search_host if wait else lib.uhnsw_search_host_async
+        _check(fn(self._h, _np_ptr(q), _np_ptr(p), _np_ptr(k_a), _np_ptr(ef_a), nq, k_max,
+                  ef_default, C.byref(o), _np_ptr(ids), _np_ptr(dist), _stream_ptr(stream)))
         return ids, dist
 
     def verify(self, q, p, cand, k: int, *, mode: str = "exact", kappa: int = 0, tau: float = 0.0,
