@@ -539,7 +539,8 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   TeamShape sh{0, 0};
   WarpShape wsh{0, 0, 0};
   const bool have_block = pick_shape(idx->tdtype, chunks, &sh);
-  const bool have_warp = pick_warp_shape(idx->tdtype, chunks, opts.team_lanes, &wsh);
+  const bool few = nq < (int64_t)idx->num_sms * WarpMinBlocks<float>::value * kWarpsPerBlock;
+  const bool have_warp = pick_warp_shape(idx->tdtype, chunks, opts.team_lanes, few, &wsh);
   if (want_warp ? !have_warp : !have_block)
     return fail(UHNSW_ECAPACITY, "uhnsw_search: no kernel shape for d=%d", idx->d);
   // warp kernel: the FP32 rows being verified are staged sv at a time (a
@@ -1104,7 +1105,7 @@ extern "C" int uhnsw_autotune(uhnsw_index* idx, const float* q, const float* p, 
   else vgs = {1, 2, 4};
   for (int team : {8, 16, 32}) {
     WarpShape ws;
-    if (!pick_warp_shape(idx->tdtype, chunks, team, &ws)) continue;
+    if (!pick_warp_shape(idx->tdtype, chunks, team, false, &ws)) continue;
     for (int rows : {4, 8, 16})
       for (int hb : hbs)
         for (int vg : vgs) {

@@ -25,9 +25,12 @@ struct WarpShape {
   int team, cpl, u;
 };
 constexpr int kWarpsPerBlock = 4;
+// The warp kernel's team shape for rows of `chunks` 16-byte chunks.
 // team_pref 0: the narrowest compiled team that covers the row; else the
-// first covering shape with exactly that many lanes.
-bool pick_warp_shape(uhnsw_dtype dt, int chunks, int team_pref, WarpShape* out);
+// first covering shape with exactly that many lanes.  `few`: the batch has
+// fewer queries than the GPU has warp slots (WarpMinBlocks blocks of
+// kWarpsPerBlock warps per SM).
+bool pick_warp_shape(uhnsw_dtype dt, int chunks, int team_pref, bool few, WarpShape* out);
 cudaError_t launch_wsearch(uhnsw_dtype dt, WarpShape sh, const QueryArgs& a, int grid,
                            size_t smem, cudaStream_t st);
 int wsearch_occupancy(uhnsw_dtype dt, WarpShape sh, size_t smem);

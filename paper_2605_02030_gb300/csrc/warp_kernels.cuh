@@ -954,12 +954,11 @@ __global__ void __launch_bounds__(WARPS * 32) uhnsw_wverify_kernel(const QueryAr
 // WARPS independent queries per block; a.queue_head set = persistent (each
 // warp pulls the next query index), else query = blockIdx.x * WARPS + warp.
 //
-// Blocks per SM asked of the register allocator: 6 (up to 85 registers, 24
-// queries per SM).  With the default shapes (FP16/BF16: 8 lanes x 2 chunks x
-// 3 rows per team; FP32: 16 x 2 x 4) this is free of spills, and it measured
-// faster than 8 blocks at 64 registers, whose spill traffic reached DRAM
-// (1.83 vs 1.99 ms and 2.31 vs 2.74 ms per 10,000 queries on 1M x 128).  The
-// smaller shared-memory carve-out also leaves a larger L1 for the rows.
+// Blocks per SM asked of the register allocator: 6 (80 registers, 24 queries
+// per SM).  It measured faster than 8 blocks at 64 registers, whose spill
+// traffic reached DRAM (1.83 vs 1.99 ms and 2.31 vs 2.74 ms per 10,000
+// queries on 1M x 128), and than 7 blocks at 72 registers.  The smaller
+// shared-memory carve-out also leaves a larger L1 for the rows.
 #ifdef UHNSW_WARP_MINB
 template <typename T>
 struct WarpMinBlocks {

@@ -140,3 +140,25 @@ def test_host_async_on_two_streams_equals_sync(setup):
     with pytest.raises(ValueError):
         idx.search_host(ins[0][0], ins[0][1], k=10, ef=40, wait=False)
     assert idx.device_status() == 0
+
+
+@pytest.mark.parametrize("width", [1, 2])
+def test_batch_size_shape_changes_no_result(setup, width):
+    """A batch with at least as many queries as the GPU has warp slots runs
+    2 rows per team and round, a smaller one 3 rows; every row's sum takes
+    the same order either way, so the results are identical."""
+    U, idx, q, pd, _ = setup
+    slots = torch.cuda.get_device_properties(0).multi_processor_count * 24
+    reps = slots // q.shape[0] + 1
+    big_q = q.repeat(reps, 1)
+    big_p = pd.repeat(reps)
+    assert big_q.shape[0] >= slots
+    ids_b, d_b, _ = idx.search(big_q, big_p, k=10, ef=48, width=width, persistent=True)
+    ids_s, d_s, _ = idx.search(q, pd, k=10, ef=48, width=width, persistent=True)
+    torch.cuda.synchronize()
+    ids_b = ids_b.cpu().numpy().reshape(reps, q.shape[0], 10)
+    d_b = d_b.cpu().numpy().reshape(reps, q.shape[0], 10)
+    for r in range(reps):
+        np.testing.assert_array_equal(ids_b[r], ids_s.cpu().numpy())
+        np.testing.assert_array_equal(d_b[r], d_s.cpu().numpy())
+    assert idx.device_status() == 0
