@@ -157,7 +157,9 @@ typedef struct {
                             fit runs the block kernel. */
   int32_t* stats;        /* device [nq][UHNSW_NSTATS] int32, or NULL */
   int32_t stage_bytes;   /* warp kernel: shared memory per query for the FP32 rows being
-                            verified (a multiple of 4 rows); 0 => 4 rows */
+                            verified (a multiple of 4 rows); 0 => as many rows as fit in
+                            the visited table's bytes (the two share one region), a
+                            multiple of 4 from 4 to 16 */
   int32_t team_lanes;    /* warp kernel: lanes sharing one row (8, 16 or 32); 0 => the
                             narrowest compiled team that covers the row */
   void* kernel_events;   /* NULL, or a host array of two cudaEvent_t that uhnsw_search
@@ -182,8 +184,9 @@ typedef struct {
                             shared memory from other queries. */
   int32_t verify_groups; /* verification in the warp-per-query kernels: 32-dimension
                             groups accumulated between two tests of a candidate's partial
-                            sum against the running k-th best sum, 1..16; 0 => 1 (the
-                            block-per-query kernel tests after every group).  Every lane
+                            sum against the running k-th best sum, 1..16; 0 => 2 in
+                            uhnsw_search, 1 in uhnsw_verify (the block-per-query kernel
+                            tests after every group).  Every lane
                             accumulates its elements in the same order whatever the
                             value, so sums and results do not depend on it; it trades
                             drop-test work for candidates summed further before they are

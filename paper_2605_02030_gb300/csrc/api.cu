@@ -544,9 +544,10 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   if (want_warp ? !have_warp : !have_block)
     return fail(UHNSW_ECAPACITY, "uhnsw_search: no kernel shape for d=%d", idx->d);
   // warp kernel: the FP32 rows being verified are staged sv at a time (a
-  // multiple of the 4 teams of a warp)
+  // multiple of the 4 teams of a warp); by default as many as fit in the
+  // launch's visited table (the two share one region), 4 to 16
   const int vrow = idx->d_pad * 4;
-  const int sv = std::max(4, (opts.stage_bytes > 0 ? opts.stage_bytes / vrow : 4) & ~3);
+  const int sv_asked = opts.stage_bytes > 0 ? std::max(4, (opts.stage_bytes / vrow) & ~3) : 0;
   constexpr size_t kSmemMax = 227 * 1024;
 
   QueryArgs& a = P->a;
@@ -578,7 +579,9 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
   a.cutoff = opts.cutoff > 0.f ? opts.cutoff : 1.4f;
   a.mode = opts.verify_mode;
   a.width = width;
-  a.vgroups = opts.verify_groups > 0 ? opts.verify_groups : 1;
+  // a drop test every 2 groups by default (measured 1 % faster than every
+  // group at 1M x 128, ef 52)
+  a.vgroups = opts.verify_groups > 0 ? opts.verify_groups : 2;
   a.vcap = 0;
   a.out_ids = out_ids;
   a.out_dist = out_dist;
@@ -605,6 +608,8 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
     bool w = want_warp;
     for (int attempt = 0; attempt < 2; ++attempt) {
       const int cmax = std::max({width * deg0, deg, w ? 4 : kBlock / 8});
+      const int sv = sv_asked > 0 ? sv_asked
+                                  : std::min(16, std::max(4, (((1 << Lo->a.hash_bits) * 4) / vrow) & ~3));
       const int stage = w ? sv * vrow : 0;
       const SmemLayout Lw(idx->d_pad, bound, Lo->a.hash_bits, cmax, k_max, 0, stage);
       const size_t smem = w ? (size_t)Lw.total * kWarpsPerBlock : (size_t)Lw.total;

@@ -369,12 +369,13 @@ def test_autotune_picks_a_valid_configuration(U, search_case, tmp_path):
 
 
 def test_table_size_and_drop_interval_change_no_result(U, search_case, qt):
-    """The autotuner's visited-table size and drop-test interval leave every
-    sum and decision of the search unchanged: any allowed table size (from
-    the smallest that holds a beam plus one step of candidates) and a drop
-    test every 1 to 5 verification groups return the default call's ids and
-    distances bit for bit, in both verification modes, and so does the
-    verification-only entry point.  A table below the minimum is refused."""
+    """The autotuner's visited-table size, drop-test interval and staged
+    verification rows leave every sum and decision of the search unchanged:
+    any allowed table size (from the smallest that holds a beam plus one
+    step of candidates), a drop test every 1 to 5 verification groups and 4
+    or 16 staged rows return the default call's ids and distances bit for
+    bit, in both verification modes, and so does the verification-only entry
+    point.  A table below the minimum is refused."""
     import math
 
     cname, w, base, qs, p, g1, g2 = search_case
@@ -391,6 +392,13 @@ def test_table_size_and_drop_interval_change_no_result(U, search_case, qt):
                                  hash_bits=hb, verify_groups=vg)
                 torch.cuda.synchronize()
                 assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1]), (mode, hb, vg)
+        if qt == 32:
+            # the staged verification rows at once (default: what the table's bytes hold)
+            for rows in (4, 16):
+                got = idx.search(q, pp, k=10, ef=ef, width=width, mode=mode, query_threads=qt,
+                                 stage_bytes=rows * 4 * base.shape[1])
+                torch.cuda.synchronize()
+                assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1]), (mode, rows)
     with pytest.raises(U.UHNSWError):
         idx.search(q, pp, k=10, ef=ef, width=width, query_threads=qt, hash_bits=lo - 1)
     cand = torch.from_numpy(np.stack([np.random.default_rng(i).choice(len(base), 60, replace=False)
