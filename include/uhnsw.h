@@ -25,7 +25,8 @@
  *   - Device work is queued on the caller's stream (a cudaStream_t passed as
  *     void*, NULL = legacy default stream); results are valid once that
  *     stream has synchronised.  Calls on one index may be queued on several
- *     streams concurrently unless stated otherwise.
+ *     streams concurrently, and from several host threads on one stream,
+ *     unless stated otherwise.
  *   - Order of results: ascending by (distance, id).  Missing results are
  *     padded with id -1 and distance +inf.
  *   - Every device wait inside the library is bounded; a wait that gives up

@@ -107,8 +107,10 @@ struct uhnsw_index {
   // counters and cursors, bucket slots, the order array); a workspace that
   // grows keeps its old buffer alive until the index is freed, since CUDA
   // graphs captured on that stream still point at it.  The host-buffer
-  // searches' device staging, with a lock that keeps one call's copies,
-  // search and copies back together on the stream.
+  // searches' device staging.  A lock that keeps one call's work together
+  // on the stream (queue reset, ordering, search; the copies of a
+  // host-buffer search), so that calls from several host threads on one
+  // stream do not interleave.
   struct StreamState {
     void* stream = nullptr;
     int32_t* head = nullptr;
@@ -116,7 +118,7 @@ struct uhnsw_index {
     int64_t cap = 0;
     void* stage = nullptr;
     size_t stage_bytes = 0;
-    std::mutex host_mu;
+    std::mutex mu;
   };
   std::vector<std::unique_ptr<StreamState>> streams;
   std::vector<void*> retired;
@@ -405,6 +407,7 @@ struct Prepared {
   cudaEvent_t events[2] = {nullptr, nullptr};  // opts.kernel_events, if given
   int32_t* qhead = nullptr;  // the stream's queue (persistent search)
   int32_t* qws = nullptr;
+  uhnsw_index::StreamState* qstate = nullptr;
   std::vector<Launch> launches;
 };
 
@@ -651,6 +654,7 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
     if (rq != UHNSW_OK) return rq;
     P->qhead = qu->head;
     P->qws = qu->ws;
+    P->qstate = qu;
     for (int b = P->bb.n - 1; b >= 0; --b) {
       Launch Lb;
       const int rc = describe(P->bb.bound[b], &Lb);
@@ -707,6 +711,10 @@ extern "C" int uhnsw_search(uhnsw_index* idx, const float* q, const float* p, co
                           &P);
   if (rc != UHNSW_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
+  // a persistent search's queue reset, ordering and launch stay together on
+  // the stream when several host threads search on it
+  std::unique_lock<std::mutex> qlock;
+  if (P.qstate) qlock = std::unique_lock<std::mutex>(P.qstate->mu);
   // A plain cudaEventRecord inside a stream capture only marks a dependency
   // (it records nothing when the graph runs), so timed calls skip the graph.
   if (!opts || !opts->use_graph || opts->kernel_events || nq == 0)
@@ -784,7 +792,7 @@ int search_host_impl(const char* fn, uhnsw_index* idx, const float* q, const flo
   int rc = stream_state(idx, stream, &ss);
   if (rc != UHNSW_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  std::lock_guard<std::mutex> lock(ss->host_mu);
+  std::lock_guard<std::mutex> lock(ss->mu);
   if (need > ss->stage_bytes) {
     // the stream's earlier searches may still read the old staging
     cudaError_t e = ss->stage ? cudaStreamSynchronize(st) : cudaSuccess;

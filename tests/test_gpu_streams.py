@@ -162,3 +162,35 @@ def test_batch_size_shape_changes_no_result(setup, width):
         np.testing.assert_array_equal(ids_b[r], ids_s.cpu().numpy())
         np.testing.assert_array_equal(d_b[r], d_s.cpu().numpy())
     assert idx.device_status() == 0
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_threads_sharing_one_stream(setup, use_graph):
+    """Persistent searches issued from several host threads on one stream
+    keep each call's queue reset, ordering and launch together: every
+    result equals the slice searched alone."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    U, idx, q, pd, _ = setup
+    ref_ids, ref_d = _alone(idx, q, pd, 40, width=2)
+    st = torch.cuda.Stream()
+    parts = [slice(a, a + 150) for a in (0, 150, 300, 450)]
+    outs = {}
+
+    def work(j):
+        sl = parts[j]
+        for r in range(5):
+            out = (torch.empty((150, 10), dtype=torch.int64, device="cuda"),
+                   torch.empty((150, 10), dtype=torch.float32, device="cuda"))
+            idx.search(q[sl], pd[sl], k=10, ef=40, width=2, persistent=True,
+                       use_graph=use_graph, stream=st, out=out)
+            outs[(j, r)] = out
+
+    torch.cuda.synchronize()
+    with ThreadPoolExecutor(max_workers=4) as ex:
+        list(ex.map(work, range(4)))
+    torch.cuda.synchronize()
+    for (j, r), (ids, dist) in outs.items():
+        np.testing.assert_array_equal(ids.cpu().numpy(), ref_ids[parts[j]], err_msg=f"{j} {r}")
+        np.testing.assert_array_equal(dist.cpu().numpy(), ref_d[parts[j]], err_msg=f"{j} {r}")
+    assert idx.device_status() == 0
