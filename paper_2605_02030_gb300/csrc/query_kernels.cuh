@@ -249,18 +249,46 @@ __device__ __forceinline__ void dist_batch(const T* __restrict__ rows, int d_pad
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       float acc = 0.0f;
+      if constexpr (VEC == 8 && (METRIC == UHNSW_BASE_L1 || METRIC == UHNSW_BASE_L2)) {
+        // 16-bit rows, L1 / L2: paired FP32 subtracts (and squares), even and
+        // odd elements accumulated apart, then added
+        uint64_t acc2 = 0;  // (+0.0f, +0.0f)
+        float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        float x[VEC];
-        unpack16<T>(buf[u][c], x);
+        for (int c = 0; c < CPL; ++c) {
+          float x[VEC];
+          unpack16<T>(buf[u][c], x);
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-          const float df = x[e] - qv[c][e];
-          if (METRIC == UHNSW_BASE_L1) acc += fabsf(df);
-          else if (METRIC == UHNSW_BASE_L05) acc += hw_sqrt(fabsf(df));
-          else if (METRIC == UHNSW_BASE_L15) acc += fabsf(df) * hw_sqrt(fabsf(df));
-          else if (METRIC == UHNSW_BASE_LP) acc += hw_ex2(bp * hw_lg2(fabsf(df)));
-          else acc = fmaf(df, df, acc);
+          for (int e = 0; e < VEC / 2; ++e) {
+            const uint64_t df = f2_sub(f2_pack(x[2 * e], x[2 * e + 1]),
+                                       f2_pack(qv[c][2 * e], qv[c][2 * e + 1]));
+            if (METRIC == UHNSW_BASE_L1) {
+              float lo, hi;
+              asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(df));
+              a0 += fabsf(lo);
+              a1 += fabsf(hi);
+            } else {
+              acc2 = f2_fma(df, df, acc2);
+            }
+          }
+        }
+        acc = METRIC == UHNSW_BASE_L1 ? a0 + a1 : f2_hsum(acc2);
+      } else {
+        // (braced: a loop pragma right after a bare `else` of an
+        // `if constexpr` made the front end drop the statement after it)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          float x[VEC];
+          unpack16<T>(buf[u][c], x);
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) {
+            const float df = x[e] - qv[c][e];
+            if (METRIC == UHNSW_BASE_L1) acc += fabsf(df);
+            else if (METRIC == UHNSW_BASE_L05) acc += hw_sqrt(fabsf(df));
+            else if (METRIC == UHNSW_BASE_L15) acc += fabsf(df) * hw_sqrt(fabsf(df));
+            else if (METRIC == UHNSW_BASE_LP) acc += hw_ex2(bp * hw_lg2(fabsf(df)));
+            else acc = fmaf(df, df, acc);
+          }
         }
       }
 #pragma unroll
@@ -545,12 +573,13 @@ __device__ void run_query(const QueryArgs& a, int64_t qi, unsigned char* smem, c
   {
     const int lt = tid % TEAM;
 #pragma unroll
-    for (int c = 0; c < CPL; ++c)
+    for (int c = 0; c < CPL; ++c) {
 #pragma unroll
       for (int e = 0; e < VEC; ++e) {
         const int idx = (lt + c * TEAM) * VEC + e;
         qv[c][e] = idx < a.d_pad ? qs[idx] : 0.f;
       }
+    }
   }
   const T* trav = reinterpret_cast<const T*>(a.trav);
   int nb = 0, nadj = 0, nexp = 0, nres = 0;

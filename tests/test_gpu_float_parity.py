@@ -19,9 +19,11 @@ no such comparison takes exactly the oracle's decisions; so:
 
 tol is twice the FP32 summation error bound of the kernel's team shape
 (each distance goes through at most CPL*VEC/2 + log2(TEAM) + 2 roundings:
-the per-lane chain over its chunks, the pair sum, the team butterfly and the
-term itself), with a 25 % margin.  The shape is fixed by asking for the team
-width."""
+the per-lane chain of even / odd pairs over its chunks, the pair sum, the
+team butterfly and the term itself), with a 25 % margin.  Both search
+kernels sum 16-bit rows this way: the warp-per-query kernel with the team
+width asked for, the block-per-query kernel with its own first covering
+shape."""
 import math
 
 import numpy as np
@@ -54,11 +56,11 @@ def _tie_tol(team, cpl, vec=8):
     return 2.0 * gamma * 1.25
 
 
-# (workload, n, nq, traversal dtype, rounding, team lanes, chunks per lane of
-# that team's first covering shape)
+# (workload, n, nq, traversal dtype, rounding, team lanes and chunks per lane
+# of the warp kernel's shape for that team, and of the block kernel's shape)
 CASES = [
-    pytest.param("gist1m", 12000, 40, "bf16", _bf16_rows, 32, 4, id="gist960_bf16"),
-    pytest.param("unit10m", 20000, 64, "f16", _f16_rows, 8, 2, id="unit96_f16"),
+    pytest.param("gist1m", 12000, 40, "bf16", _bf16_rows, (32, 4), (32, 4), id="gist960_bf16"),
+    pytest.param("unit10m", 20000, 64, "f16", _f16_rows, (8, 2), (16, 1), id="unit96_f16"),
 ]
 
 
@@ -70,9 +72,11 @@ def built():
     return U
 
 
-@pytest.mark.parametrize("name,n,nq,dt,rnd,team,cpl", CASES)
+@pytest.mark.parametrize("name,n,nq,dt,rnd,wshape,bshape", CASES)
 @pytest.mark.parametrize("width", [1, 2])
-def test_precision_form_float_data_id_parity(built, name, n, nq, dt, rnd, team, cpl, width):
+@pytest.mark.parametrize("kernel", ["warp", "block"])
+def test_precision_form_float_data_id_parity(built, name, n, nq, dt, rnd, wshape, bshape, width,
+                                             kernel):
     U = built
     w = I.WORKLOADS[name].scaled(n=n, nq=nq)
     base = I.base_vectors(w)
@@ -83,11 +87,13 @@ def test_precision_form_float_data_id_parity(built, name, n, nq, dt, rnd, team, 
     g1 = U.build_graph(base, 1, 16, 100, I.graph_levels(w, 1), threads=0)
     g2 = U.build_graph(base, 2, 16, 100, I.graph_levels(w, 2), threads=0)
     idx = U.Index(base, g1, g2, traverse_dtype=dt)
+    team, cpl = wshape if kernel == "warp" else bshape
     tol = _tie_tol(team, cpl)
     ef, k = 64, 10
     q = torch.from_numpy(qs).cuda()
     holders = (oracle._CSRHolder(g1), oracle._CSRHolder(g2))
-    opts = dict(query_threads=32, team_lanes=team, width=width)
+    opts = (dict(query_threads=32, team_lanes=team, width=width) if kernel == "warp" else
+            dict(query_threads=128, width=width))
 
     tie_free = diverged = flagged_diverged = verify_tie_diverged = 0
     # Algorithm 1 for each query's own p (general p), and p = 1 / 2 with the
@@ -126,7 +132,7 @@ def test_precision_form_float_data_id_parity(built, name, n, nq, dt, rnd, team, 
                     flagged_diverged += 1
             diverged += int(not same)
     total = 3 * nq
-    print(f"{name} width {width}: {tie_free}/{total} searches tie-free (checked id for id); "
+    print(f"{name} {kernel} width {width}: {tie_free}/{total} searches tie-free (checked id for id); "
           f"{diverged} answers differ from the oracle: {flagged_diverged} after a near-tie of "
           f"the search (tol {tol:.2e}), {verify_tie_diverged} by an L_p near-tie of the "
           f"verification (1e-5)")
