@@ -768,6 +768,111 @@ def run_workload(args, log):
     print(json.dumps(workload_record(args, log, args.workload, sized=True)), flush=True)
 
 
+def _small_config_record(args, log, w, idx, q_dev, p_dev, gt, deg0, pipe, l2_note):
+    """mixture10k (10,000 x 32 FP32 rows, 100 queries with p ~ U(0.5, 2],
+    k = 10, ef = 64): plain U-HNSW on the FP32 rows.  Its rows and graphs
+    (about 4 MB) stay in L2, so the roof is the L2 gather rate for 128-byte
+    rows, probed in the same run.  The configuration's own batch of 100
+    queries occupies 100 warps of the GPU's 3,648: its launch time is a
+    latency.  Throughput and roofline are taken on the same queries tiled
+    100 times (10,000 per launch, queued like the headline's steps)."""
+    import torch
+    from paper_2605_02030_gb300 import uhnsw as U
+
+    k, ef, nq = 10, w.ef, q_dev.shape[0]
+    lat = []
+    for i in range(args.warmup + max(10, args.steps)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ids, dist, _ = idx.search(q_dev, p_dev, k=k, ef=ef)
+        b.record()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            lat.append(a.elapsed_time(b))
+    ids = ids.cpu().numpy()
+    p = p_dev.cpu().numpy()
+    hits = _recall_at_k(ids, gt, np.full(nq, k))
+    bins = I.p_bin_of(w, p)
+
+    reps = 100
+    tq, tp = q_dev.repeat(reps, 1).contiguous(), p_dev.repeat(reps).contiguous()
+    nt = tq.shape[0]
+    outs = [(torch.empty((nt, k), dtype=torch.int64, device="cuda"),
+             torch.empty((nt, k), dtype=torch.float32, device="cuda")) for _ in pipe]
+
+    def step(i):
+        st = pipe[i % len(pipe)]
+        with torch.cuda.stream(st):
+            idx.search(tq, tp, k=k, ef=ef, persistent=True, use_graph=True, stream=st,
+                       out=outs[i % len(pipe)])
+
+    for i in range(args.warmup * len(pipe)):
+        step(i)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(pipe[0])
+        for st in pipe[1:]:
+            st.wait_event(a)
+        for i in range(args.steps):
+            step(i)
+        for st in pipe[1:]:
+            e = torch.cuda.Event()
+            e.record(st)
+            pipe[0].wait_event(e)
+        b.record(pipe[0])
+        torch.cuda.synchronize()
+    step_ms = a.elapsed_time(b) / args.steps
+    tiled_ids = outs[(args.steps - 1) % len(pipe)][0].cpu().numpy().reshape(reps, nq, k)
+    same = bool((tiled_ids == ids[None]).all())
+    _, _, st = idx.search(tq, tp, k=k, ef=ef, persistent=True, stats=True)
+    st = st.cpu().numpy().astype(np.int64)
+    alg = int((st[:, 0] * w.d * 4).sum() + (st[:, 7] * deg0 * 4).sum() + (st[:, 2] * 4).sum()
+              + nt * (w.d * 4 + 4 + 12 * k))
+    l2buf = torch.empty(48 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda").fill_(1.0)
+    l2_peak = 0.0
+    for _ in range(3):
+        ms, nb = U.probe_gather(l2buf, w.d * 4, per_warp=1024, blocks_per_sm=8)
+        l2_peak = max(l2_peak, nb / (ms / 1e3))
+    del l2buf
+    ach = alg / (step_ms / 1e3)
+    value = 1e3 * nt / step_ms
+    log(f"mixture10k: 100-query launch {statistics.median(lat):.4f} ms; tiled "
+        f"{value / 1e6:.3f} M queries/s, {ach / 1e9:.1f} of {l2_peak / 1e9:.1f} GB/s (L2)")
+    return {
+        "metric": "plain U-HNSW, FP32, 10k x 32: QPS and launch latency (L2-resident)",
+        "value": round(value, 1), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"mixture10k: N={w.n:,} d={w.d} FP32, {w.n_clusters}-centre "
+                               f"Gaussian mixture; {nq} queries, p ~ U(0.5,2], k={k}, ef={ef}; "
+                               f"G1/G2 M={w.M} efConstruction={w.ef_construction}",
+                   "form": "FP32 traversal rows (plain U-HNSW), exact verification",
+                   "config_batch": {"queries": nq,
+                                    "launch_ms_median": round(statistics.median(lat), 4),
+                                    "launch_ms_min": round(min(lat), 4),
+                                    "qps": round(1e3 * nq / statistics.median(lat), 1),
+                                    "timing": "CUDA events around each plain launch"},
+                   "value_batch": f"the {nq} queries tiled {reps} times ({nt:,} per launch), "
+                                  f"persistent launch with CUDA-graph replay; every copy "
+                                  f"returns the batch's own ids: {same}",
+                   "l2": l2_note,
+                   "recall_at_10": round(float(hits.mean()), 4),
+                   "recall_at_10_min_p_bin": round(min(float(hits[bins == bb].mean())
+                                                       for bb in np.unique(bins)), 4),
+                   "stats_per_query": {"N_b": float(st[:, 0].mean()),
+                                       "N_p": float(st[:, 1].mean())}},
+        "roofline": {"bound": "l2", "achieved": round(ach / 1e9, 1),
+                     "peak": round(l2_peak / 1e9, 1), "unit": "GB/s",
+                     "frac": round(ach / l2_peak, 4), "traffic": None,
+                     "algorithmic_bytes_per_launch": alg, "launch_ms": round(step_ms, 4),
+                     "peak_source": "uhnsw_probe_gather: random 128-byte rows of a warmed "
+                                    "48 MB buffer, best of 3, this run (of measured)"},
+        "clocks": clk.summary(),
+        "gpu_launches": args.steps * 3,
+    }
+
+
 def workload_record(args, log, name, sized=False):
     """The batched form on the GIST-shaped 1M x 960 workload (BF16 rows, each
     query with its own p, k and ef), the serving form on the 10M x 96
@@ -789,7 +894,8 @@ def workload_record(args, log, name, sized=False):
     qs = I.query_vectors(w)
     p, kq, efq = I.query_params(w)
     log(f"inputs {w.n}x{w.d}, {w.nq} queries in {time.time() - t0:.1f} s")
-    g1, g2 = graphs_for(w, base, log, device="cpu" if name == "sift1m_e" else "gpu")
+    g1, g2 = graphs_for(w, base, log,
+                        device="cpu" if name in ("sift1m_e", "mixture10k") else "gpu")
     idx = U.Index(base, g1, g2, traverse_dtype=w.traverse_dtype, metrics=w.metrics)
     q_dev = torch.from_numpy(qs).cuda()
     p_dev = torch.from_numpy(p).cuda()
@@ -894,6 +1000,13 @@ def workload_record(args, log, name, sized=False):
                 "single_launch": {"launch_ms": round(kern_ms, 4), "achieved": round(single, 1),
                                   "frac": round(single / peak, 4)},
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+    if name == "mixture10k":
+        line = _small_config_record(args, log, w, idx, q_dev, p_dev, gt, deg0, pipe,
+                                    "L2-resident (about 4 MB of rows and graphs); steps queued "
+                                    "back to back on %d streams" % len(pipe))
+        idx.close()
+        return line
 
     if name == "gist1m":
         k_dev = torch.from_numpy(kq).cuda()
@@ -1534,7 +1647,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the full-size records of the other workloads in the default run")
-    ap.add_argument("--extras", default="gist1m,unit10m",
+    ap.add_argument("--extras", default="mixture10k,gist1m,unit10m",
                     help="workloads recorded after the headline (comma-separated)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-ef", type=int, default=52,
@@ -1556,7 +1669,7 @@ def main():
     ap.add_argument("--query-threads", type=int, default=32, choices=(32, 128),
                     help="32: warp-per-query kernel, 128: block-per-query kernel")
     ap.add_argument("--workload", default="sift1m",
-                    choices=("sift1m", "gist1m", "unit10m", "sift1m_e"),
+                    choices=("sift1m", "gist1m", "unit10m", "sift1m_e", "mixture10k"),
                     help="sift1m: the headline line; gist1m: the batched form on 1M x 960 BF16; "
                          "unit10m: the serving form on 10M x 96 FP16; sift1m_e: U-HNSW-E")
     ap.add_argument("--idealized", action="store_true",
