@@ -161,8 +161,9 @@ typedef struct {
                             verified (a multiple of 4 rows); 0 => as many rows as fit in
                             the visited table's bytes (the two share one region), a
                             multiple of 4 from 4 to 16 */
-  int32_t team_lanes;    /* warp kernel: lanes sharing one row (8, 16 or 32); 0 => the
-                            narrowest compiled team that covers the row */
+  int32_t team_lanes;    /* warp kernel: lanes sharing one row (4, 8, 16 or 32); 0 => the
+                            default shape for the row's width (e.g. 4 lanes x 3 chunks
+                            for 96 FP16 dimensions, 8 x 2 for 128) */
   void* kernel_events;   /* NULL, or a host array of two cudaEvent_t that uhnsw_search
                             records on its stream right before the first search-kernel
                             launch and right after the last one: the search kernels' own

@@ -492,8 +492,10 @@ int prepare_search(uhnsw_index* idx, const float* q, const float* p, const int32
                 kBlock);
   if (opts.ef_max < 0 || opts.ef_max > UHNSW_MAX_EF)
     return fail(UHNSW_EINVAL, "uhnsw_search: ef_max=%d", opts.ef_max);
-  if (opts.team_lanes != 0 && opts.team_lanes != 8 && opts.team_lanes != 16 && opts.team_lanes != 32)
-    return fail(UHNSW_EINVAL, "uhnsw_search: team_lanes=%d not 0, 8, 16 or 32", opts.team_lanes);
+  if (opts.team_lanes != 0 && opts.team_lanes != 4 && opts.team_lanes != 8 &&
+      opts.team_lanes != 16 && opts.team_lanes != 32)
+    return fail(UHNSW_EINVAL, "uhnsw_search: team_lanes=%d not 0, 4, 8, 16 or 32",
+                opts.team_lanes);
   if (opts.stage_bytes < 0 || opts.stage_bytes > 64 * 1024)
     return fail(UHNSW_EINVAL, "uhnsw_search: stage_bytes=%d not in [0, 65536]", opts.stage_bytes);
   if (opts.hash_bits < 0 || opts.hash_bits > 15)
@@ -1116,7 +1118,7 @@ extern "C" int uhnsw_autotune(uhnsw_index* idx, const float* q, const float* p, 
   else hbs = {0};
   if (b.verify_groups > 0) vgs = {b.verify_groups};
   else vgs = {1, 2, 4};
-  for (int team : {8, 16, 32}) {
+  for (int team : {4, 8, 16, 32}) {
     WarpShape ws;
     if (!pick_warp_shape(idx->tdtype, chunks, team, false, &ws)) continue;
     for (int rows : {4, 8, 16})

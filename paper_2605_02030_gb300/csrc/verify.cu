@@ -165,15 +165,20 @@ bool pick_warp_shape(uhnsw_dtype dt, int chunks, int team_pref, bool few, WarpSh
   // small to fill the GPU's warps (`few`) is bound by each query's own
   // latency: there three rows per round keep more loads in flight (serving
   // batches of 7 to 33 queries: p50 7 % and p99 up to 25 % lower than with
-  // two rows).  The shape never changes a result.
+  // two rows).  Rows of 12 chunks (96 FP16 dimensions) take 4 lanes x 3
+  // chunks, which leaves no lane on a zeroed chunk: 3.5 % faster than
+  // 8 x 2 at 10M x 96, ef 512.  The shape never changes a result.
   static const WarpShape f32[] = {{8, 1, 4},  {8, 2, 2},  {16, 2, 4}, {32, 2, 2},
                                   {32, 4, 2}, {32, 8, 1}, {32, 16, 1}};
-  static const WarpShape f16[] = {{8, 1, 4},  {8, 2, 2},  {16, 2, 2}, {32, 2, 2},
-                                  {32, 4, 2}, {32, 8, 1}, {32, 16, 1}};
-  static const WarpShape f16_few[] = {{8, 1, 4},  {8, 2, 3},  {16, 2, 2}, {32, 2, 2},
-                                      {32, 4, 2}, {32, 8, 1}, {32, 16, 1}};
+  static const WarpShape f16[] = {{8, 1, 4},  {4, 3, 2},  {8, 2, 2},  {16, 2, 2},
+                                  {32, 2, 2}, {32, 4, 2}, {32, 8, 1}, {32, 16, 1}};
+  static const WarpShape f16_few[] = {{8, 1, 4},  {4, 3, 2},  {8, 2, 3},  {16, 2, 2},
+                                      {32, 2, 2}, {32, 4, 2}, {32, 8, 1}, {32, 16, 1}};
   const WarpShape* list = dt == UHNSW_F32 ? f32 : few ? f16_few : f16;
-  for (int i = 0; i < 7; ++i)
+  const int cnt = dt == UHNSW_F32 ? (int)(sizeof(f32) / sizeof(f32[0]))
+                                  : (int)(sizeof(f16) / sizeof(f16[0]));
+  static_assert(sizeof(f16) == sizeof(f16_few), "the two 16-bit lists have one length");
+  for (int i = 0; i < cnt; ++i)
     if (list[i].team * list[i].cpl >= chunks && (team_pref == 0 || list[i].team == team_pref)) {
       *out = list[i];
       return true;

@@ -32,6 +32,7 @@ int wocc_one(size_t smem) {
   do {                                                                       \
     const int key_ = (SH).team * 1000 + (SH).cpl * 10 + (SH).u;              \
     switch (key_) {                                                          \
+      case 4032: return CALL(T, 4, 3, 2);                                    \
       case 8014: return CALL(T, 8, 1, 4);                                    \
       case 8022: return CALL(T, 8, 2, 2);                                    \
       case 8023: return CALL(T, 8, 2, 3);                                    \

@@ -60,7 +60,7 @@ def _tie_tol(team, cpl, vec=8):
 # of the warp kernel's shape for that team, and of the block kernel's shape)
 CASES = [
     pytest.param("gist1m", 12000, 40, "bf16", _bf16_rows, (32, 4), (32, 4), id="gist960_bf16"),
-    pytest.param("unit10m", 20000, 64, "f16", _f16_rows, (8, 2), (16, 1), id="unit96_f16"),
+    pytest.param("unit10m", 20000, 64, "f16", _f16_rows, (4, 3), (16, 1), id="unit96_f16"),
 ]
 
 
