@@ -26,7 +26,10 @@
  *     void*, NULL = legacy default stream); results are valid once that
  *     stream has synchronised.  Calls on one index may be queued on several
  *     streams concurrently, and from several host threads on one stream,
- *     unless stated otherwise.
+ *     unless stated otherwise.  The index keeps a small state for every
+ *     stream that has searched it (persistent-queue counters and ordering
+ *     workspace, host-search staging) until uhnsw_free: reuse a fixed set
+ *     of streams rather than a new stream per call.
  *   - Order of results: ascending by (distance, id).  Missing results are
  *     padded with id -1 and distance +inf.
  *   - Every device wait inside the library is bounded; a wait that gives up
