@@ -1678,7 +1678,8 @@ def main():
     ap.add_argument("--workload", default="sift1m",
                     choices=("sift1m", "gist1m", "unit10m", "sift1m_e", "mixture10k"),
                     help="sift1m: the headline line; gist1m: the batched form on 1M x 960 BF16; "
-                         "unit10m: the serving form on 10M x 96 FP16; sift1m_e: U-HNSW-E")
+                         "unit10m: the serving form on 10M x 96 FP16; sift1m_e: U-HNSW-E; "
+                         "mixture10k: the 10k x 32 FP32 configuration against the L2 roof")
     ap.add_argument("--idealized", action="store_true",
                     help="Section 3.2's idealized-recall experiment and a recall-targeted t per p")
     ap.add_argument("--target", type=float, default=0.97,
