@@ -1472,6 +1472,8 @@ def run_profile(args, log):
     from paper_2605_02030_gb300 import uhnsw as U
 
     pkg.build()
+    if args.workload == "gist1m":
+        return _profile_run_gist(args, log)
     w = workload(args)
     base = I.base_vectors(w)
     qs = I.query_vectors(w)
@@ -1493,6 +1495,51 @@ def run_profile(args, log):
             ms.append(a.elapsed_time(b))
     print(json.dumps({"profile_run": f"{w.name} ef={ef} width={width}",
                       "ms_median": round(statistics.median(ms), 4)}), flush=True)
+    idx.close()
+
+
+def _profile_run_gist(args, log):
+    """--profile-run --workload gist1m [--n N]: the GIST-shaped batched form
+    (BF16 rows, each query with its own p, k and ef) on the block-per-query
+    kernel with the default visited table, three warm-up searches and --steps
+    searches, L2 flushed before each.  Each search launches the two
+    queue-ordering kernels, then one search launch per beam bucket (<= 64,
+    128, 256, 512), largest first."""
+    import torch
+    from paper_2605_02030_gb300 import uhnsw as U
+
+    w = I.WORKLOADS["gist1m"]
+    if args.n:
+        w = w.scaled(n=args.n)
+    base = I.base_vectors(w)
+    qs = I.query_vectors(w)
+    p, kq, efq = I.query_params(w)
+    g1, g2 = graphs_for(w, base, log, device="gpu")
+    idx = U.Index(base, g1, g2, traverse_dtype=w.traverse_dtype)
+    q, pd = torch.from_numpy(qs).cuda(), torch.from_numpy(p).cuda()
+    kd, efd = torch.from_numpy(kq).cuda(), torch.from_numpy(efq).cuda()
+    k_max, ef_max = int(kq.max()), int(efq.max())
+    flush = torch.empty(384 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ms = []
+    for i in range(3 + args.steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        idx.search(q, pd, k=kd, ef=efd, k_max=k_max, ef_max=ef_max, persistent=True,
+                   query_threads=128)
+        b.record()
+        torch.cuda.synchronize()
+        if i >= 3:
+            ms.append(a.elapsed_time(b))
+    _, _, st = idx.search(q, pd, k=kd, ef=efd, k_max=k_max, ef_max=ef_max, persistent=True,
+                          query_threads=128, stats=True)
+    st = st.cpu().numpy().astype(np.int64)
+    alg = int((st[:, 0] * w.d * 2).sum() + (st[:, 7] * g1["max_degree0"] * 4).sum()
+              + (st[:, 2] * 4).sum() + w.nq * (w.d * 4 + 4 + 12 * k_max))
+    print(json.dumps({"profile_run": f"{w.name} n={w.n} block kernel, per-query k / ef",
+                      "ms_median": round(statistics.median(ms), 4),
+                      "algorithmic_bytes_per_search": alg,
+                      "N_b": float(st[:, 0].mean())}), flush=True)
     idx.close()
 
 
